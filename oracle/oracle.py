@@ -1,0 +1,210 @@
+"""ctypes front end of the SymPix oracle (plain FP64 C, ``sympix_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU baseline / reference arm of ``bench.py``.  The library package
+never imports this module; the CUDA path and the oracle share no code.
+
+Every function is a thin marshalling layer over one C function; the C file
+states which passage of the paper each one follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "sympix_oracle.c"
+_LIB = _HERE / "liboracle.so"
+
+_dptr = ctypes.POINTER(ctypes.c_double)
+_i32ptr = ctypes.POINTER(ctypes.c_int32)
+_i64ptr = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (IEEE FP64, no FMA contraction)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".so.tmp{os.getpid()}")
+        subprocess.run(
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+             "-o", str(tmp), str(_SRC), "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(_LIB))
+        L.sympix_oracle_kernel_u.restype = ctypes.c_double
+        L.sympix_oracle_kernel_u.argtypes = [ctypes.c_int, _dptr, ctypes.c_double]
+        L.sympix_oracle_gl_theta.argtypes = [ctypes.c_int, _dptr]
+        L.sympix_oracle_gl_weights.argtypes = [ctypes.c_int, _dptr, _dptr]
+        L.sympix_oracle_layout_greedy.argtypes = [ctypes.c_int, _dptr, _i32ptr]
+        L.sympix_oracle_layout_dp.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              _dptr, _i32ptr, _i32ptr]
+        L.sympix_oracle_u.restype = ctypes.c_double
+        L.sympix_oracle_u.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_long,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_long]
+        L.sympix_oracle_coupled.argtypes = [_dptr, _i32ptr, ctypes.c_int, ctypes.c_long,
+                                            ctypes.c_int, ctypes.c_double, _i32ptr]
+        L.sympix_oracle_block.restype = ctypes.c_long
+        L.sympix_oracle_block.argtypes = [ctypes.c_int, _dptr, _i32ptr, _i64ptr, _i32ptr,
+                                          ctypes.c_int, _dptr, _dptr, ctypes.c_double,
+                                          _dptr, ctypes.c_int, _dptr]
+        L.sympix_oracle_cholesky.argtypes = [ctypes.c_int, _dptr, _dptr]
+        L.sympix_oracle_ordering.restype = ctypes.c_long
+        L.sympix_oracle_ordering.argtypes = [ctypes.c_int, ctypes.c_int, _i32ptr, _i64ptr, _i32ptr]
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# -- grid ---------------------------------------------------------------------
+
+def gl_theta(N: int) -> np.ndarray:
+    """Ring colatitudes theta_j (north to south), roots of P_N(cos theta)."""
+    th = np.empty(N, dtype=np.float64)
+    if lib().sympix_oracle_gl_theta(N, _p(th, _dptr)) != 0:
+        raise ValueError("bad ring count")
+    return th
+
+
+def gl_weights(theta: np.ndarray) -> np.ndarray:
+    th = _f64(theta)
+    w = np.empty_like(th)
+    lib().sympix_oracle_gl_weights(len(th), _p(th, _dptr), _p(w, _dptr))
+    return w
+
+
+def layout_greedy(lmax: int, theta: np.ndarray) -> np.ndarray:
+    th = _f64(theta)
+    n = np.zeros(lmax + 1, dtype=np.int32)
+    lib().sympix_oracle_layout_greedy(lmax, _p(th, _dptr), _p(n, _i32ptr))
+    return n
+
+
+def dp_nrings(lmax: int, k: int) -> int:
+    N = lmax + 1
+    if N % (2 * k):
+        N += 2 * k - N % (2 * k)
+    return N
+
+
+def layout_dp(lmax: int, k: int, thr: float, theta: np.ndarray):
+    """Tiles per northern band T_i and the bound alpha_i (Fig. Optimal-SymPix-Grid)."""
+    th = _f64(theta)
+    nb = len(th) // (2 * k)
+    T = np.zeros(nb, dtype=np.int32)
+    alpha = np.zeros(nb, dtype=np.int32)
+    rc = lib().sympix_oracle_layout_dp(lmax, k, float(thr), _p(th, _dptr), _p(T, _i32ptr),
+                                       _p(alpha, _i32ptr))
+    if rc != 0:
+        raise ValueError("no DP layout satisfies the constraints")
+    return T, alpha
+
+
+def ordering(N: int, k: int, nring: np.ndarray):
+    nr = np.ascontiguousarray(nring, dtype=np.int32)
+    off = np.zeros(N, dtype=np.int64)
+    stride = np.zeros(N, dtype=np.int32)
+    npix = lib().sympix_oracle_ordering(N, k, _p(nr, _i32ptr), _p(off, _i64ptr), _p(stride, _i32ptr))
+    if npix < 0:
+        raise ValueError("ring counts do not form bands of k rings")
+    return off, stride, int(npix)
+
+
+def grid(lmax: int, k: int = 1, layout: str = "greedy", thr: float = -1.0) -> dict:
+    """The whole grid: theta, per-ring counts, pixel numbering."""
+    if layout == "greedy":
+        if k != 1:
+            raise ValueError("the greedy layout has k = 1")
+        N = lmax + 1
+        theta = gl_theta(N)
+        nring = layout_greedy(lmax, theta)
+    elif layout == "dp":
+        N = dp_nrings(lmax, k)
+        theta = gl_theta(N)
+        T, _ = layout_dp(lmax, k, thr, theta)
+        nb = N // (2 * k)
+        nring = np.zeros(N, dtype=np.int32)
+        for i in range(nb):
+            for r in range(k):
+                nring[i * k + r] = k * T[i]
+                nring[N - 1 - i * k - r] = k * T[i]
+    else:
+        raise ValueError(layout)
+    off, stride, npix = ordering(N, k, nring)
+    return dict(lmax=lmax, k=k, nrings=N, theta=theta, nring=nring,
+                ring_offset=off, ring_stride=stride, npix=npix)
+
+
+# -- kernel values and support -----------------------------------------------
+
+def kernel_u(lmax: int, cl: np.ndarray, u) -> np.ndarray:
+    """Eq. addition-theorem at x = 1 - u (vectorised over u by a Python loop)."""
+    c = _f64(cl)
+    assert len(c) >= lmax + 1
+    f = lib().sympix_oracle_kernel_u
+    uu = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    return np.array([f(lmax, _p(c, _dptr), float(x)) for x in uu])
+
+
+def pair_u(theta1: float, n1: int, c1: int, theta2: float, n2: int, c2: int) -> float:
+    return lib().sympix_oracle_u(float(theta1), int(n1), int(c1), float(theta2), int(n2), int(c2))
+
+
+def coupled(g: dict, j: int, c: int, rho: int, r_s: float) -> np.ndarray:
+    out = np.zeros(int(g["nring"][rho]), dtype=np.int32)
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    cnt = lib().sympix_oracle_coupled(_p(th, _dptr), _p(nr, _i32ptr), int(j), int(c), int(rho),
+                                      float(r_s), _p(out, _i32ptr))
+    return out[:cnt].copy()
+
+
+# -- blocks -------------------------------------------------------------------
+
+def block(g: dict, bl: np.ndarray, dl: np.ndarray, r_s: float, ninv: np.ndarray, j: int):
+    """Dense preconditioner block of ring j and the number of triples summed."""
+    n = int(g["nring"][j])
+    M = np.zeros((n, n), dtype=np.float64)
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    off = np.ascontiguousarray(g["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g["ring_stride"], dtype=np.int32)
+    b = _f64(bl)
+    d = _f64(dl)
+    nv = _f64(ninv)
+    assert len(nv) == g["npix"]
+    triples = lib().sympix_oracle_block(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr),
+                                        _p(off, _i64ptr), _p(st, _i32ptr), g["lmax"],
+                                        _p(b, _dptr), _p(d, _dptr), float(r_s),
+                                        _p(nv, _dptr), int(j), _p(M, _dptr))
+    return M, int(triples)
+
+
+def cholesky(A: np.ndarray):
+    """Lower Cholesky factor and LAPACK-style info (0, or first bad row + 1)."""
+    A = _f64(A)
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    info = lib().sympix_oracle_cholesky(n, _p(A, _dptr), _p(L, _dptr))
+    return L, int(info)
