@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Throughput of SymPix preconditioner blocks on one GB300 (or N, weak scaling).
+
+A step is one pass of the whole hot path over one operator at l_max = 3000,
+FWHM 5': kernel table (FP64) -> block sampling D^ + B^T N^-1 B^ -> FP64
+Cholesky of every block.  The headline `value` is the mixed path (FP32
+contraction); the FP64 and split-FP32 contractions are timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own independent problem (the inverse-noise
+map of rank r uses seed 4 + r), so the per-GPU work is fixed as N grows.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "preconditioner block elements/s at l_max=3000: mixed vs FP64, % of roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL = 1.25e12   # dense FP64 FLOP/s, GB300 nominal (recipe table)
+FP32_NOMINAL = 152 * 128 * 2 * 2.07e9  # FP32 FMA lanes x 2 x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lmax3000")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32x2", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--arms", default="fp64,fp32x2", help="extra contraction arms timed beside the headline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# -- oracle sample (CPU baseline and reference arm) ---------------------------------------
+
+def oracle_rings(og, nmax=2048, count=16, shift=0):
+    """A bounded sample: `count` rings spread over the polar caps whose rings
+    hold <= nmax pixels (the oracle's dense Cholesky is O(n^3) per ring)."""
+    cand = [j for j in range(og["nrings"]) if og["nring"][j] <= nmax]
+    idx = np.linspace(0, len(cand) - 1, count).round().astype(int)
+    return [cand[(i + shift) % len(cand)] for i in idx]
+
+
+def run_oracle_sample(wl, og, ninv, rings, threads):
+    from oracle import oracle as O
+
+    def one(j):
+        M, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv, j)
+        L, info = O.cholesky(M)
+        n = M.shape[0]
+        q = np.arange(n)
+        nz = np.nonzero(M)
+        if len(nz[0]):
+            dist = np.minimum((nz[0] - nz[1]) % n, (nz[1] - nz[0]) % n)
+            w = int(dist.max())
+        else:
+            w = 0
+        return n * (w + 1) if 2 * w + 1 < n else n * (n + 1) // 2
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        elems = list(ex.map(one, rings))
+    dt = time.perf_counter() - t0
+    return int(sum(elems)), dt
+
+
+# -- clocks ----------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].strip() not in ("", "[N/A]")),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# -- the GPU arm ---------------------------------------------------------------------------
+
+def factor_flops(plan):
+    tot = 0.0
+    for o in range(plan.nops):
+        for j in range(plan.ring0, plan.ring1):
+            _, n, w, fmt = plan.block_layout("pband", o, j)
+            if fmt == 0:
+                m = n - w
+                tot += 2.0 * (m * w * (w + 1) / 2 + w * m * w + n * w * (w + 1) / 2) + 2.0 * n
+            else:
+                tot += n ** 3 / 3.0
+    return tot
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1504_04653_gb300 import sympix as S
+    from paper_1504_04653_gb300 import workloads as W
+
+    wl = W.WORKLOADS[args.workload]
+    wl = W.Workload(wl.name, wl.lmax, wl.fwhm_arcmin, wl.band_deg, [s + rank for s in wl.seeds], wl.desc)
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    nbytes, elements = plan.blocks_size("pband")
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    ninv_h = wl.ninv(colat)
+    bl_h, dl_h = wl.beams(), wl.priors()
+    bl = torch.tensor(bl_h, dtype=torch.float64, device=dev)
+    dl = torch.tensor(dl_h, dtype=torch.float64, device=dev)
+    ninv = torch.tensor(ninv_h, dtype=torch.float64, device=dev)
+    blocks = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+    info = torch.empty(plan.nblocks, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(prec, ev=None):
+        if ev:
+            ev[0].record(stream)
+        S.sympix_kernel_table(plan, bl, dl, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        S.sympix_sample_blocks(plan, ninv, precision=prec, storage="pband", out=blocks, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        S.sympix_factor_blocks(plan, blocks, storage="pband", info=info, stream=stream)
+        if ev:
+            ev[3].record(stream)
+
+    def timed(prec, K, W_):
+        with torch.cuda.stream(stream):
+            for _ in range(W_):
+                step(prec)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))          # evict L2 between steps (outside the events)
+                step(prec, evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        st = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(3)] for k in range(K)])
+        return st, wall
+
+    clocks = Clocks(local)
+    main_st, main_wall = timed(args.precision, args.steps, args.warmup)
+    clk = clocks.stop()
+    info_h = info.cpu().numpy()
+    sampled_main = None
+    ms_step = float(main_st.sum(axis=1).mean())
+    ms_max = ms_step
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * elements / (ms_max * 1e-3)
+
+    # other contraction arms (same steps) and their accuracy against FP64
+    arms = {}
+    ref64 = None
+    for prec in [a for a in args.arms.split(",") if a and a != args.precision]:
+        st, _ = timed(prec, args.steps, 1)
+        arms[prec] = {"value": elements / (float(st.sum(axis=1).mean()) * 1e-3),
+                      "ms_per_step": float(st.sum(axis=1).mean()),
+                      "stages_ms": dict(zip(["table", "sample", "factor"], st.mean(axis=0).round(4).tolist()))}
+    # accuracy of the sampled blocks against the FP64 GPU path, normwise per block
+    acc = {}
+    if rank == 0:
+        outs = {}
+        for prec in ("fp64", args.precision, "fp32x2"):
+            with torch.cuda.stream(stream):
+                S.sympix_kernel_table(plan, bl, dl, stream=stream)
+                S.sympix_sample_blocks(plan, ninv, precision=prec, storage="pband", out=blocks, stream=stream)
+            torch.cuda.synchronize()
+            outs[prec] = blocks.clone()
+        offs = [plan.block_layout("pband", 0, j) for j in range(plan.ring0, plan.ring1)]
+        for prec in (args.precision, "fp32x2"):
+            if prec == "fp64":
+                continue
+            worst = 0.0
+            for off, n, w, fmt in offs:
+                ln = n * (w + 1) if fmt == 0 else n * n
+                a = outs[prec][off:off + ln]
+                b = outs["fp64"][off:off + ln]
+                e = float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+                worst = max(worst, e)
+            acc[f"{prec}_vs_fp64_normwise_max"] = worst
+        del outs
+
+    # e2e: the same step through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        bl_p = torch.tensor(bl_h, dtype=torch.float64).pin_memory()
+        dl_p = torch.tensor(dl_h, dtype=torch.float64).pin_memory()
+        ninv_p = torch.tensor(ninv_h, dtype=torch.float64).pin_memory()
+        out_p = torch.empty(nbytes // 8, dtype=torch.float64).pin_memory()
+        info_p = torch.empty(plan.nblocks, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            bl.copy_(bl_p, non_blocking=True)
+            dl.copy_(dl_p, non_blocking=True)
+            ninv.copy_(ninv_p, non_blocking=True)
+            step(args.precision)
+            out_p.copy_(blocks, non_blocking=True)
+            info_p.copy_(info, non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        h2d = (bl_p.numel() + dl_p.numel() + ninv_p.numel()) * 8
+        d2h = out_p.numel() * 8 + info_p.numel() * 4
+        e2e = {"value": world * elements / (ms * 1e-3), "unit": "elements/s", "ms_per_step": ms,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant kernel
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0) * 1e9
+    stages = dict(zip(["table", "sample", "factor"], main_st.mean(axis=0).tolist()))
+    dominant = max(stages, key=stages.get)
+    L = wl.lmax
+    table_flops = plan.nslots * plan.nops * (L - 1) * 7.0
+    sample_flops = 2.0 * plan.ntriples + plan.nmults
+    sample_bytes = elements * 8 + grid.npix * 8 * plan.nops
+    if dominant == "table":
+        roof = {"kernel": "k_table", "bound": "alu", "achieved": table_flops / (stages["table"] * 1e-3) / 1e12,
+                "peak": FP64_NOMINAL / 1e12, "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    elif dominant == "factor":
+        ff = factor_flops(plan)
+        roof = {"kernel": "k_factor", "bound": "alu", "achieved": ff / (stages["factor"] * 1e-3) / 1e12,
+                "peak": FP64_NOMINAL / 1e12, "unit": "TFLOP/s", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    else:
+        t_hbm = sample_bytes / hbm
+        t_alu = sample_flops / FP32_NOMINAL
+        if t_hbm >= t_alu:
+            roof = {"kernel": "k_sample_pband", "bound": "hbm",
+                    "achieved": sample_bytes / (stages["sample"] * 1e-3) / 1e9, "peak": hbm / 1e9,
+                    "unit": "GB/s", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        else:
+            roof = {"kernel": "k_sample_pband", "bound": "alu",
+                    "achieved": sample_flops / (stages["sample"] * 1e-3) / 1e12, "peak": FP32_NOMINAL / 1e12,
+                    "unit": "TFLOP/s", "peak_source": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["stage_ms"] = stages[dominant]
+
+    launches = sum(plan.launches("pband"))
+    line = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 contraction, f64 kernel table and Cholesky",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "lmax": wl.lmax, "fwhm_arcmin": wl.fwhm_arcmin[0], "nops": plan.nops,
+                   "npix": int(grid.npix), "elements": int(elements), "storage": "pband",
+                   "precision": args.precision, "triples": int(plan.ntriples), "kernel_slots": int(plan.nslots),
+                   "l2": "256 MB buffer written between steps, outside the step events",
+                   "parallelism": f"independent problem per GPU x{world}"},
+        "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+        "arms": arms, "accuracy": acc, "roofline": roof, "e2e": e2e,
+        "gpu_launches": launches * args.steps, "clocks": clk,
+        "all_blocks_factored": bool((info_h == 0).all()),
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        og = O.grid(wl.lmax)
+        rings = oracle_rings(og)
+        threads = min(16, os.cpu_count() or 1)
+        el, dt = run_oracle_sample(wl, og, ninv_h[0], rings, threads)
+        line["cpu_baseline"] = {"value": el / dt, "unit": "elements/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{len(rings)} polar-cap rings (n <= 2048) of the same workload, "
+                                          f"one thread each: {el} elements in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1504_04653_gb300 import workloads as W
+    O.build()
+    wl = W.WORKLOADS[args.workload]
+    og = O.grid(wl.lmax)
+    colat = W.pixel_colatitude(og["theta"], og["nring"], og["ring_offset"], og["ring_stride"], og["npix"])
+    ninv = wl.ninv(colat)[0]
+    threads = min(16, os.cpu_count() or 1)
+    for s in range(args.warmup):
+        run_oracle_sample(wl, og, ninv, oracle_rings(og, count=threads, shift=s), threads)
+    tot_el, tot_t = 0, 0.0
+    for s in range(args.steps):
+        el, dt = run_oracle_sample(wl, og, ninv, oracle_rings(og, count=threads, shift=1000 + s), threads)
+        tot_el += el
+        tot_t += dt
+    v = tot_el / tot_t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "lmax": wl.lmax, "fwhm_arcmin": wl.fwhm_arcmin[0]},
+        "cpu_baseline": {"value": v, "unit": "elements/s", "cores": threads, "kind": "oracle",
+                         "sample": f"per step {threads} polar-cap rings (n <= 2048), one thread each"},
+        "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * sympix.h -- C ABI of the GB300 SymPix preconditioner-block library.
+ *
+ * The library samples the rotationally invariant operators D^ = Y D Y^T and
+ * B^ = Y B Y^T in pixel space on a SymPix grid and forms, per ring, the
+ * preconditioner block  M = D^ + B^T N^-1 B^  (Seljebotn & Eriksen,
+ * "SymPix: a spherical grid for efficient sampling of rotationally
+ * invariant operators", Sec. 4.2, Eq. system-rewritten and Eq. Dhat), then
+ * Cholesky-factors every block.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns SYMPIX_OK (0) or a positive error code; the text of
+ *     the last error of the calling thread is sympix_last_error().  No call
+ *     aborts the process.
+ *   - Device pointers are plain CUDA device addresses of the current device;
+ *     host pointers are ordinary host memory.  The caller owns every pointer
+ *     it passes; the library owns the handles it returns and frees them in
+ *     the matching *_free call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it and return;
+ *     their launch errors are reported at once, device-side failures of the
+ *     factorisation through the per-block `info` array.
+ *   - Indices: rings j = 0 .. nrings-1 run north to south; the pixels of
+ *     ring j are columns c = 0 .. n_j-1 at longitude 2 pi (c + 1/2) / n_j.
+ *   - There is no CPU fallback: if no CUDA device is usable every compute
+ *     call fails with SYMPIX_ECUDA.
+ */
+#ifndef SYMPIX_H
+#define SYMPIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SYMPIX_OK 0
+#define SYMPIX_EINVAL 1   /* bad argument (size, range, null pointer)         */
+#define SYMPIX_ENOMEM 2   /* a device or host allocation of the library failed */
+#define SYMPIX_ECUDA 3    /* a CUDA call failed (message names it)             */
+#define SYMPIX_ETIMEOUT 4 /* a bounded device wait ran out                      */
+#define SYMPIX_EUNSUPPORTED 5 /* combination not implemented (message says which) */
+
+/* grid layouts */
+#define SYMPIX_LAYOUT_GREEDY 0 /* per-ring counts, k = 1, N_rings = lmax + 1      */
+#define SYMPIX_LAYOUT_DP 1     /* bands of k rings chosen by dynamic programming  */
+
+/* arithmetic of the B^T N^-1 B^ contraction */
+#define SYMPIX_PREC_FP64 0   /* FP64 products and sums                           */
+#define SYMPIX_PREC_FP32 1   /* FP32 products, FP32 accumulation                 */
+#define SYMPIX_PREC_FP32X2 2 /* split FP32 (hi + lo pairs): near-FP64 on FP32 pipes */
+
+/* block storage */
+#define SYMPIX_STORE_PBAND 0 /* periodic band + border, dense for small rings   */
+#define SYMPIX_STORE_DENSE 1 /* every block n x n                              */
+
+/* block formats reported by sympix_block_layout */
+#define SYMPIX_BLOCK_PBAND 0
+#define SYMPIX_BLOCK_DENSE 1
+
+typedef struct sympix_grid_s *sympix_grid_t;
+typedef struct sympix_plan_s *sympix_plan_t;
+
+typedef struct {
+    int lmax;       /* band limit the grid was built for                    */
+    int k;          /* tile size (rings per band)                            */
+    int layout;     /* SYMPIX_LAYOUT_*                                       */
+    int nrings;     /* number of rings                                       */
+    int nbands;     /* number of bands of k rings (an odd equator ring counts as one) */
+    int max_ring;   /* largest ring pixel count                              */
+    int64_t npix;   /* number of pixels                                      */
+} sympix_grid_desc;
+
+/* ------------------------------------------------------------------------ */
+/* Grid (Sec. 2; Fig. Optimal-SymPix-Grid)                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Build a SymPix grid.
+ *   lmax       band limit (>= 1, <= 16383).
+ *   k          tile size: 1 for SYMPIX_LAYOUT_GREEDY; >= 1 for SYMPIX_LAYOUT_DP.
+ *   layout     SYMPIX_LAYOUT_GREEDY: N_rings = lmax + 1, per-ring counts from
+ *              the equator outward, target 2 (lmax+1) sin theta_j, neighbour
+ *              ratios in {1, 6/5, 5/4, 4/3, 2, 3}, at least 8 per ring.
+ *              SYMPIX_LAYOUT_DP: the dynamic programme of Fig.
+ *              Optimal-SymPix-Grid (Sec. 2.5) with N_rings = lmax + 1 rounded
+ *              up to a multiple of 2k.
+ *   polar_thr  threshold of Eq. polar-optimization (Sec. 2.1); < 0 selects
+ *              the paper's max(100, lmax/100).  Ignored by GREEDY.
+ *   out        receives a library-owned handle (free with sympix_grid_free).
+ * Ring colatitudes are the roots of P_{N_rings}(cos theta) (Sec. 1, 2.1),
+ * found on the device in FP64.  Pixel numbering (Sec. 2.4): bands of k rings
+ * in the order north 0, south 0, north 1, south 1, ...; inside a band the
+ * index runs fastest along theta; a southern band counts its rings from its
+ * pole; an odd equatorial ring (GREEDY) comes last.  Synchronous. */
+int sympix_grid(int lmax, int k, int layout, double polar_thr, sympix_grid_t *out);
+
+/* Sizes of a grid. */
+int sympix_grid_describe(sympix_grid_t grid, sympix_grid_desc *desc);
+
+/* Copy the ring tables to host arrays of length nrings (any may be NULL):
+ * theta[j] colatitude, nring[j] pixel count, ring_offset[j] index of the
+ * ring's pixel c = 0, ring_stride[j] index step between its columns (pixel
+ * c of ring j is ring_offset[j] + c * ring_stride[j]). */
+int sympix_grid_copy(sympix_grid_t grid, double *theta, int32_t *nring,
+                     int64_t *ring_offset, int32_t *ring_stride);
+
+void sympix_grid_free(sympix_grid_t grid);
+
+/* ------------------------------------------------------------------------ */
+/* Support, symmetry classes and block plan (Eq. f; Sec. 2.3; Sec. 4.2)     */
+/* ------------------------------------------------------------------------ */
+
+/* Plan `nops` operators on `grid` for the blocks of rings [ring0, ring1).
+ *   r_s   host array [nops]: support radius (radians) of operator o; a pixel
+ *         pair couples when its angular distance is <= r_s[o] (the truncation
+ *         of Eq. f, one radius for D^ and B^ of the operator).  r_s >= pi
+ *         couples every pair.
+ * The device computes, for every coupled pair of rings, the distinct pixel
+ * separations (one symmetry class per distinct |phi_1 - phi_2|, shared by
+ * the transposed and the north/south-mirrored ring pair) and the band width
+ * of every block; the host-side plan keeps the block sizes and offsets.
+ * Only GREEDY grids (k = 1; one ring per block) can be planned.
+ * Allocates the class and kernel tables on the device.  Synchronous.
+ * out receives a library-owned handle (free with sympix_plan_free). */
+int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, int ring1,
+                   sympix_plan_t *out);
+
+/* Counts of a plan (any pointer may be NULL): nslots symmetry-class slots
+ * (kernel values per operator); npairs coupled ordered ring pairs summed over
+ * operators; ntriples the pixel triples (q, r, p) with r in the stored lower
+ * band of q and p coupled to both, summed over all periodic-band blocks (the
+ * algorithmic multiply-adds of the B^T N^-1 B^ contraction); nmults the
+ * products B^_pq N^-1_p formed once per coupled pair (q, p). */
+int sympix_plan_counts(sympix_plan_t plan, int64_t *nslots, int64_t *npairs, int64_t *ntriples,
+                       int64_t *nmults);
+
+/* Number of kernel launches one call of sympix_kernel_table,
+ * sympix_sample_blocks (for `storage`) and sympix_factor_blocks enqueues. */
+int sympix_plan_launches(sympix_plan_t plan, int storage, int32_t *table, int32_t *sample,
+                         int32_t *factor);
+
+/* Output size of sample/factor for a storage mode: bytes of the blocks
+ * buffer (doubles) and the number of stored lower-triangle elements
+ * (periodic band including the diagonal; n (n+1) / 2 for dense blocks). */
+int sympix_blocks_size(sympix_plan_t plan, int storage, size_t *bytes, int64_t *elements);
+
+/* Where block (op, ring) sits in the blocks buffer of a storage mode:
+ * offset in doubles, ring size n, lower band half-width w, format
+ * SYMPIX_BLOCK_PBAND or SYMPIX_BLOCK_DENSE.
+ *   PBAND format: n (2w+1) doubles.  Sampled: band[q*(w+1) + d] =
+ *   M[q][(q-d) mod n] for d = 0..w (the other entries follow by symmetry).
+ *   Factored: with m = n - w, rows i < m of L as band[i*(w+1)+d] = L[i][i-d]
+ *   (d <= min(i, w)); rows m..n-1 of L in the border that follows the band,
+ *   border[(i-m)*n + c] = L[i][c] for c <= i.
+ *   DENSE format: n*n doubles, row-major M; factored: L in the lower
+ *   triangle (the strict upper triangle keeps M). */
+int sympix_block_layout(sympix_plan_t plan, int storage, int op, int ring, int64_t *offset,
+                        int32_t *n, int32_t *w, int32_t *format);
+
+/* Per coupled ring pair (ring j of a planned block, neighbour ring rho):
+ * the largest coupled separation index m (pixel pairs with
+ * |(2c+1) n_rho - (2p+1) n_j| / gcd(n_j, n_rho) <= m couple), written for
+ * every rho in [ring - radius, ring + radius] into mmax[rho - ring + radius]
+ * (-1 where nothing couples).  For tests and diagnostics. */
+int sympix_support_copy(sympix_plan_t plan, int op, int ring, int radius, int32_t *mmax);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel table (Eq. addition-theorem)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Evaluate b(x) = sum_l (2l+1)/(4 pi) b_l P_l(x) at every symmetry-class
+ * slot of every operator, and d(x) likewise at the same-ring slots.
+ *   bl, dl  device arrays [nops][lmax+1] of b_l and d_l (row o = operator o).
+ * FP64, O(lmax) per slot (Sec. 4.2).  Writes the plan's kernel tables; must
+ * precede sympix_sample_blocks.  Asynchronous on `stream`. */
+int sympix_kernel_table(sympix_plan_t plan, const double *bl, const double *dl, void *stream);
+
+/* Copy operator `op`'s kernel values to the host: b at every slot of ring
+ * pair (ring, rho) for separation indices m = par, par+2, ..., mmax
+ * (par = mmax mod 2), count values; d likewise for rho == ring (NULL to
+ * skip).  Synchronous.  For tests. */
+int sympix_table_copy(sympix_plan_t plan, int op, int ring, int rho, int count, double *b,
+                      double *d);
+
+/* ------------------------------------------------------------------------ */
+/* Blocks (Eq. Dhat, Eq. system-rewritten)                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Sample every planned block  M = D^_jj + sum_p B^_pq N^-1_p B^_pr  (q, r on
+ * ring j, p over all pixels; Y2 = Y1) for every operator.
+ *   ninv       device [nops][npix] inverse noise N^-1 in pixel numbering.
+ *   precision  SYMPIX_PREC_*: arithmetic of the contraction (the kernel
+ *              values are FP64 in every mode; outputs are FP64).
+ *   storage    SYMPIX_STORE_*.
+ *   blocks     device buffer of sympix_blocks_size(storage) bytes.
+ * One grouped launch covers every (operator, block, tile).  Asynchronous. */
+int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, int storage,
+                         double *blocks, void *stream);
+
+/* Cholesky-factor every sampled block in place, M = L L^T, in FP64.
+ *   info  device int32 [nops * nblocks] (operator-major, blocks in ring
+ *         order): 0, or i+1 for the first row i whose pivot is not positive
+ *         (that block's factor is then incomplete).
+ * Asynchronous. */
+int sympix_factor_blocks(sympix_plan_t plan, int storage, double *blocks, int32_t *info,
+                         void *stream);
+
+void sympix_plan_free(sympix_plan_t plan);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *sympix_last_error(void);
+
+/* Library version string. */
+const char *sympix_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYMPIX_H */

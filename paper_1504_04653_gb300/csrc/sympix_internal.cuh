@@ -1,0 +1,146 @@
+// Internal types shared by the translation units of libsympix.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sympix.h"
+
+namespace sympix {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// -- errors ------------------------------------------------------------------
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+
+#define SPX_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t e__ = (call);                             \
+        if (e__ != cudaSuccess) return cuda_error(e__, #call); \
+    } while (0)
+
+// Device buffer owned by a handle.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    int alloc(size_t count) {
+        release();
+        if (count == 0) return SYMPIX_OK;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            return set_error(SYMPIX_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                             cudaGetErrorString(e));
+        }
+        n = count;
+        return SYMPIX_OK;
+    }
+    int upload(const std::vector<T> &v) {
+        int rc = alloc(v.size());
+        if (rc) return rc;
+        if (!v.empty()) SPX_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return SYMPIX_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+};
+
+}  // namespace sympix
+
+// -- grid ---------------------------------------------------------------------
+struct sympix_grid_s {
+    int lmax = 0, k = 1, layout = 0, nrings = 0, nbands = 0, max_ring = 0;
+    int64_t npix = 0;
+    std::vector<double> theta;          // ring colatitudes, north to south
+    std::vector<int32_t> nring, stride; // pixels per ring; column step in the numbering
+    std::vector<int64_t> offset;        // pixel index of column 0
+    sympix::DevBuf<double> d_theta;
+};
+
+// One coupled ordered ring pair (ring j of a block, neighbour ring rho).
+// Pixel c of ring j and pixel p of ring rho are at separation index
+// z = (2c+1) Q - (2p+1) P, with P = n_j / g, Q = n_rho / g, g = gcd; they
+// couple iff |z| <= mmax, and their kernel value is table[tab + (|z|-par)/2].
+struct PairEntry {
+    int32_t rho;
+    int32_t P, Q;
+    int32_t mmax;
+    int32_t par;
+    int32_t nrho;
+    int32_t nstride;
+    int32_t pad;
+    int64_t tab;
+    int64_t noff;
+};
+
+// One planned block (operator op, ring ring).
+struct BlockDesc {
+    int32_t op, ring, n, w;
+    int32_t format;   // SYMPIX_BLOCK_PBAND / SYMPIX_BLOCK_DENSE
+    int32_t npairs;   // coupled neighbour rings
+    int64_t pair0;    // first PairEntry
+    int64_t off_pband, off_dense;  // offsets (doubles) in the two storage modes
+    int64_t dtab;     // slot of level 0 of the same-ring pair
+    int32_t dK;       // same-ring levels (D support)
+    int32_t pad;
+};
+
+// One canonical ring pair (a <= b, a <= N-1-b): the kernel values of the
+// transposed and the north/south mirrored pair are the same.
+struct CanonPair {
+    int32_t a, b;
+    int32_t na, nb;
+    int32_t g;
+    int32_t kmax;   // levels stored (max over operators)
+    int64_t slot0;  // first slot
+};
+
+// Work item of the sampling launches.
+struct SampleItem {
+    int32_t block;
+    int32_t q0;
+};
+
+struct sympix_plan_s {
+    sympix_grid_t grid = nullptr;
+    int nops = 0, ring0 = 0, ring1 = 0;
+    std::vector<double> r_s;
+    std::vector<int> radius;            // ring offset bound per operator
+    std::vector<CanonPair> pairs;       // canonical pairs
+    std::vector<int32_t> pair_mmax;     // [pair][op]
+    std::vector<BlockDesc> blocks;      // [op][ring1-ring0]
+    std::vector<PairEntry> entries;
+    int64_t nslots = 0;
+    int64_t ntriples = 0, nmults = 0;
+    int64_t elems_pband = 0, elems_dense = 0;
+    int64_t size_pband = 0, size_dense = 0;  // doubles
+    int max_w = 0;
+    // sampling schedule (built once)
+    std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
+    std::vector<SampleItem> items_dense;
+    std::vector<int32_t> factor_order;       // blocks sorted by factor cost
+    // device
+    sympix::DevBuf<CanonPair> d_pairs;
+    sympix::DevBuf<double> d_slot_u;         // u = 1 - cos(gamma) per slot
+    sympix::DevBuf<int32_t> d_slot_pair;     // canonical pair of each slot
+    sympix::DevBuf<double> d_tab_b, d_tab_d; // [op][nslots] FP64
+    sympix::DevBuf<float> d_tab_b32;         // [op][nslots] FP32 (rounded)
+    sympix::DevBuf<float> d_tab_blo;         // [op][nslots] FP32 remainder b - hi
+    sympix::DevBuf<double> d_rec;            // recurrence coefficients
+    sympix::DevBuf<BlockDesc> d_blocks;
+    sympix::DevBuf<PairEntry> d_entries;
+    sympix::DevBuf<SampleItem> d_items_pband[5];
+    sympix::DevBuf<SampleItem> d_items_dense;
+    sympix::DevBuf<int32_t> d_factor_order;
+    bool table_ready = false;
+};

@@ -1,0 +1,411 @@
+// Support, symmetry classes and block plan.
+//
+// Pixel c of ring j (n_j pixels, longitude 2 pi (c + 1/2) / n_j) and pixel p
+// of ring rho differ in longitude by pi z g / (n_j n_rho) with the integer
+// z = (2c+1) Q - (2p+1) P, P = n_j / g, Q = n_rho / g, g = gcd(n_j, n_rho).
+// Their separation therefore depends only on (j, rho, |z|): every distinct
+// |z| of a ring pair is one symmetry class (Sec. 2.3: distances repeat along
+// the ring with period P), evaluated once (Sec. 4.1, 4.2).  The transposed
+// pair (rho, j) and the north/south mirror (N-1-j, N-1-rho) have the same
+// classes, so only canonical pairs own table slots.  A pair couples when its
+// angular distance is <= r_s (the truncation of Eq. f); |z| grows with the
+// distance, so the coupled classes of a ring pair are |z| <= mmax.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <unordered_map>
+
+#include "sympix_internal.cuh"
+
+namespace sympix {
+
+// u = 1 - cos(gamma) of separation index m on canonical pair (a, b), by the
+// haversine identity 2 sin^2(dtheta/2) + 2 sin th_a sin th_b sin^2(dphi/2),
+// dphi / 2 = pi m g / (2 n_a n_b).
+__device__ __forceinline__ double class_u(double base, double st, double denom, long mg) {
+    double h = sin(0.5 * kPi * (double)mg / denom);
+    return base + st * h * h;
+}
+
+// One thread per (canonical pair, operator): the largest coupled |z|.
+__global__ void k_support_mmax(int npairs, int nops, const CanonPair *__restrict__ pairs,
+                               const double *__restrict__ theta, const double *__restrict__ rs,
+                               int32_t *__restrict__ mmax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs * nops) return;
+    const int pi = i / nops, o = i % nops;
+    const CanonPair cp = pairs[pi];
+    const long P = cp.na / cp.g, Q = cp.nb / cp.g;
+    const long PQg = P * Q * cp.g;
+    const long par = (P + Q) & 1;
+    const long mcap = PQg - ((PQg - par) & 1);  // |dphi| <= pi
+    const double r = rs[o];
+    if (r >= kPi) {
+        mmax[i] = (int32_t)mcap;
+        return;
+    }
+    const double hs = sin(0.5 * r);
+    const double us = 2.0 * hs * hs;
+    const double ta = theta[cp.a], tb = theta[cp.b];
+    const double da = sin(0.5 * (ta - tb));
+    const double base = 2.0 * da * da;
+    const double st = 2.0 * sin(ta) * sin(tb);
+    const double denom = (double)cp.na * (double)cp.nb;
+    if (class_u(base, st, denom, par * cp.g) > us) {
+        mmax[i] = -1;
+        return;
+    }
+    long m = par;
+    while (m + 2 <= mcap && class_u(base, st, denom, (m + 2) * cp.g) <= us) m += 2;
+    mmax[i] = (int32_t)m;
+}
+
+// One thread per canonical pair: u of each stored class.
+__global__ void k_support_slots(int npairs, const CanonPair *__restrict__ pairs, const double *__restrict__ theta,
+                                double *__restrict__ slot_u, int32_t *__restrict__ slot_pair) {
+    int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= npairs) return;
+    const CanonPair cp = pairs[pi];
+    const long P = cp.na / cp.g, Q = cp.nb / cp.g;
+    const long par = (P + Q) & 1;
+    const double ta = theta[cp.a], tb = theta[cp.b];
+    const double da = sin(0.5 * (ta - tb));
+    const double base = 2.0 * da * da;
+    const double st = 2.0 * sin(ta) * sin(tb);
+    const double denom = (double)cp.na * (double)cp.nb;
+    for (int k = 0; k < cp.kmax; ++k) {
+        slot_u[cp.slot0 + k] = class_u(base, st, denom, (par + 2L * k) * cp.g);
+        slot_pair[cp.slot0 + k] = pi;
+    }
+}
+
+// Largest offset d >= 0 such that some pixel couples to both c and c - d
+// (for some class c), i.e. some z = (2c+1)Q - (2p+1)P lies in
+// [2 d Q - m, m]; -1 if none.
+static long entry_width(long P, long Q, long m) {
+    long w = -1;
+    for (long d = 0;; ++d) {
+        const long lo = 2 * d * Q - m;
+        if (lo > m) break;
+        for (long c = 0; c < P; ++c) {
+            long z0 = ((2 * c + 1) * Q - P) % (2 * P);
+            if (z0 < 0) z0 += 2 * P;
+            long r = ((z0 - lo) % (2 * P) + 2 * P) % (2 * P);
+            if (lo + r <= m) {
+                w = d;
+                break;
+            }
+        }
+    }
+    return w;
+}
+
+// Work of one entry over one period of P columns: multiply-adds (pixels p
+// coupled to both c and c - d, summed over d = 0..w and c) and products
+// B^_pq N^-1_p (pixels coupled to c).
+static void entry_work(long P, long Q, long m, long w, int64_t *triples, int64_t *mults) {
+    int64_t t = 0, mu = 0;
+    for (long c = 0; c < P; ++c) {
+        long z0 = ((2 * c + 1) * Q - P) % (2 * P);
+        if (z0 < 0) z0 += 2 * P;
+        auto count = [&](long lo, long hi) -> int64_t {  // lattice points z0 + 2P k in [lo, hi]
+            if (lo > hi) return 0;
+            long first = lo + (((z0 - lo) % (2 * P)) + 2 * P) % (2 * P);
+            if (first > hi) return 0;
+            return (hi - first) / (2 * P) + 1;
+        };
+        mu += count(-m, m);
+        for (long d = 0; d <= w; ++d) t += count(2 * d * Q - m, m);
+    }
+    *triples = t;
+    *mults = mu;
+}
+
+static long gcdl(long a, long b) {
+    while (b) {
+        long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+}  // namespace sympix
+
+using namespace sympix;
+
+extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, int ring1,
+                              sympix_plan_t *out) {
+    if (!out) return set_error(SYMPIX_EINVAL, "sympix_support: out is NULL");
+    *out = nullptr;
+    if (!grid || !r_s) return set_error(SYMPIX_EINVAL, "sympix_support: NULL argument");
+    if (grid->layout != SYMPIX_LAYOUT_GREEDY || grid->k != 1)
+        return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: blocks are planned for k = 1 (greedy) grids only");
+    const int N = grid->nrings;
+    if (nops < 1 || nops > 4096) return set_error(SYMPIX_EINVAL, "sympix_support: nops %d out of [1, 4096]", nops);
+    if (ring0 < 0 || ring1 > N || ring0 >= ring1)
+        return set_error(SYMPIX_EINVAL, "sympix_support: ring range [%d, %d) not inside [0, %d)", ring0, ring1, N);
+    for (int o = 0; o < nops; ++o)
+        if (!(r_s[o] > 0.0) || !std::isfinite(r_s[o]))
+            return set_error(SYMPIX_EINVAL, "sympix_support: r_s[%d] must be positive and finite", o);
+    if (grid->max_ring > 30000)
+        return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: rings above 30000 pixels overflow 32-bit indices");
+
+    sympix_plan_s *pl = new sympix_plan_s();
+    auto fail = [&](int code) {
+        delete pl;
+        return code;
+    };
+    pl->grid = grid;
+    pl->nops = nops;
+    pl->ring0 = ring0;
+    pl->ring1 = ring1;
+    pl->r_s.assign(r_s, r_s + nops);
+    const std::vector<double> &th = grid->theta;
+    const std::vector<int32_t> &nr = grid->nring;
+    double hmin = kPi;
+    for (int j = 0; j + 1 < N; ++j) hmin = std::min(hmin, th[j + 1] - th[j]);
+    int rmax = 0;
+    for (int o = 0; o < nops; ++o) {
+        int R = (r_s[o] >= kPi) ? N : (int)std::min<double>(N, ceil(r_s[o] / hmin) + 1);
+        pl->radius.push_back(R);
+        rmax = std::max(rmax, R);
+    }
+
+    // canonical ring pairs met by the planned blocks
+    std::unordered_map<int64_t, int> index;
+    auto canon = [&](int j, int rho) {
+        int a = std::min(j, rho), b = std::max(j, rho);
+        if (a > N - 1 - b) {
+            int a2 = N - 1 - b, b2 = N - 1 - a;
+            a = a2;
+            b = b2;
+        }
+        return std::make_pair(a, b);
+    };
+    for (int j = ring0; j < ring1; ++j)
+        for (int rho = std::max(0, j - rmax); rho <= std::min(N - 1, j + rmax); ++rho) {
+            auto ab = canon(j, rho);
+            int64_t key = (int64_t)ab.first * N + ab.second;
+            if (index.count(key)) continue;
+            CanonPair cp{};
+            cp.a = ab.first;
+            cp.b = ab.second;
+            cp.na = nr[cp.a];
+            cp.nb = nr[cp.b];
+            cp.g = (int32_t)gcdl(cp.na, cp.nb);
+            index[key] = (int)pl->pairs.size();
+            pl->pairs.push_back(cp);
+        }
+    const int npairs = (int)pl->pairs.size();
+
+    // device: coupled classes per pair and operator
+    int rc;
+    DevBuf<double> d_rs;
+    DevBuf<int32_t> d_mmax;
+    {
+        std::vector<double> rsv(r_s, r_s + nops);
+        if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = d_rs.upload(rsv)) ||
+            (rc = d_mmax.alloc((size_t)npairs * nops)))
+            return fail(rc);
+        const int tot = npairs * nops;
+        k_support_mmax<<<(tot + 127) / 128, 128>>>(npairs, nops, pl->d_pairs.p, grid->d_theta.p, d_rs.p, d_mmax.p);
+        pl->pair_mmax.resize((size_t)tot);
+        cudaError_t e = cudaMemcpy(pl->pair_mmax.data(), d_mmax.p, (size_t)tot * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(cuda_error(e, "sympix_support: class search"));
+    }
+    // slots: levels 0..kmax-1 of every canonical pair (max over operators)
+    int64_t nslots = 0;
+    for (int pi = 0; pi < npairs; ++pi) {
+        CanonPair &cp = pl->pairs[pi];
+        int kmax = 0;
+        for (int o = 0; o < nops; ++o) {
+            int m = pl->pair_mmax[(size_t)pi * nops + o];
+            if (m >= 0) kmax = std::max(kmax, m / 2 + 1);
+        }
+        cp.kmax = kmax;
+        cp.slot0 = nslots;
+        nslots += kmax;
+    }
+    pl->nslots = nslots;
+    if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = pl->d_slot_u.alloc(std::max<int64_t>(nslots, 1))) ||
+        (rc = pl->d_slot_pair.alloc(std::max<int64_t>(nslots, 1))))
+        return fail(rc);
+    k_support_slots<<<(npairs + 127) / 128, 128>>>(npairs, pl->d_pairs.p, grid->d_theta.p, pl->d_slot_u.p,
+                                                   pl->d_slot_pair.p);
+
+    // blocks and their coupled neighbour rings
+    const int nb = ring1 - ring0;
+    int64_t offp = 0, offd = 0;
+    for (int o = 0; o < nops; ++o) {
+        for (int j = ring0; j < ring1; ++j) {
+            BlockDesc bd{};
+            bd.op = o;
+            bd.ring = j;
+            bd.n = nr[j];
+            bd.pair0 = (int64_t)pl->entries.size();
+            bd.dtab = -1;
+            long w = 0;
+            bool wrap = false;
+            const int R = pl->radius[o];
+            for (int rho = std::max(0, j - R); rho <= std::min(N - 1, j + R); ++rho) {
+                auto ab = canon(j, rho);
+                const int pi = index.at((int64_t)ab.first * N + ab.second);
+                const int m = pl->pair_mmax[(size_t)pi * nops + o];
+                if (m < 0) continue;
+                const long g = gcdl(nr[j], nr[rho]);
+                PairEntry pe{};
+                pe.rho = rho;
+                pe.P = (int32_t)(nr[j] / g);
+                pe.Q = (int32_t)(nr[rho] / g);
+                pe.mmax = m;
+                pe.par = (pe.P + pe.Q) & 1;
+                pe.nrho = nr[rho];
+                pe.nstride = grid->stride[rho];
+                pe.tab = pl->pairs[pi].slot0;
+                pe.noff = grid->offset[rho];
+                if ((long)m >= (long)pe.P * pe.Q * g - pe.P) wrap = true;
+                w = std::max(w, entry_width(pe.P, pe.Q, m));
+                if (rho == j) {
+                    bd.dtab = pe.tab;
+                    bd.dK = m / 2 + 1;
+                }
+                pl->entries.push_back(pe);
+            }
+            bd.npairs = (int32_t)((int64_t)pl->entries.size() - bd.pair0);
+            bd.w = (int32_t)w;
+            if (!(wrap || 2 * w + 1 >= bd.n || w > 64)) {
+                for (int e = 0; e < bd.npairs; ++e) {
+                    const PairEntry &pe = pl->entries[bd.pair0 + e];
+                    int64_t t, mu;
+                    entry_work(pe.P, pe.Q, pe.mmax, w, &t, &mu);
+                    pl->ntriples += t * (bd.n / pe.P);
+                    pl->nmults += mu * (bd.n / pe.P);
+                }
+            }
+            bd.format = (wrap || 2 * w + 1 >= bd.n || w > 64) ? SYMPIX_BLOCK_DENSE : SYMPIX_BLOCK_PBAND;
+            const int64_t n = bd.n;
+            bd.off_pband = offp;
+            bd.off_dense = offd;
+            if (bd.format == SYMPIX_BLOCK_PBAND) {
+                offp += n * (2 * w + 1);
+                pl->elems_pband += n * (w + 1);
+                pl->max_w = std::max<int>(pl->max_w, (int)w);
+            } else {
+                if (n > 8192) {
+                    return fail(set_error(SYMPIX_EUNSUPPORTED,
+                                          "sympix_support: ring %d (%d pixels) couples too widely for a band", j, bd.n));
+                }
+                offp += n * n;
+                pl->elems_pband += n * (n + 1) / 2;
+            }
+            offd += n * n;
+            pl->elems_dense += n * (n + 1) / 2;
+            pl->blocks.push_back(bd);
+        }
+    }
+    pl->size_pband = offp;
+    pl->size_dense = offd;
+
+    // sampling work items: pband blocks in tiles of 128 columns, bucketed by
+    // band width; dense blocks in tiles of 256 elements
+    for (size_t b = 0; b < pl->blocks.size(); ++b) {
+        const BlockDesc &bd = pl->blocks[b];
+        if (bd.format == SYMPIX_BLOCK_PBAND) {
+            int bucket = bd.w <= 8 ? 0 : bd.w <= 16 ? 1 : bd.w <= 32 ? 2 : 3;
+            for (int q0 = 0; q0 < bd.n; q0 += 128) pl->items_pband[bucket].push_back({(int32_t)b, q0});
+        } else {
+            const int64_t ne = (int64_t)bd.n * bd.n;
+            for (int64_t e0 = 0; e0 < ne; e0 += 256) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
+        }
+    }
+    // factorisation order: most expensive blocks first
+    pl->factor_order.resize(pl->blocks.size());
+    std::iota(pl->factor_order.begin(), pl->factor_order.end(), 0);
+    auto cost = [&](int b) {
+        const BlockDesc &bd = pl->blocks[b];
+        double n = bd.n, w = bd.w;
+        return bd.format == SYMPIX_BLOCK_PBAND ? n * (w + 1) * (3 * w + 1) : n * n * n / 3.0;
+    };
+    std::stable_sort(pl->factor_order.begin(), pl->factor_order.end(),
+                     [&](int x, int y) { return cost(x) > cost(y); });
+
+    if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
+        (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_factor_order.upload(pl->factor_order)))
+        return fail(rc);
+    for (int bkt = 0; bkt < 5; ++bkt)
+        if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
+    const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
+    if ((rc = pl->d_tab_b.alloc(tabn)) || (rc = pl->d_tab_d.alloc(tabn)) || (rc = pl->d_tab_b32.alloc(tabn)) ||
+        (rc = pl->d_tab_blo.alloc(tabn)))
+        return fail(rc);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(cuda_error(e, "sympix_support"));
+    (void)nb;
+    *out = pl;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_plan_counts(sympix_plan_t pl, int64_t *nslots, int64_t *npairs, int64_t *ntriples,
+                                  int64_t *nmults) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_counts: NULL plan");
+    if (nslots) *nslots = pl->nslots;
+    if (npairs) *npairs = (int64_t)pl->entries.size();
+    if (ntriples) *ntriples = pl->ntriples;
+    if (nmults) *nmults = pl->nmults;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int32_t *table, int32_t *sample,
+                                    int32_t *factor) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_launches: NULL plan");
+    if (table) *table = pl->nslots > 0 ? 1 + (pl->nops + 3) / 4 : 1;
+    int s = storage == SYMPIX_STORE_DENSE ? 1 : 0;  // the zero fill
+    for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
+    s += pl->items_dense.empty() ? 0 : 1;
+    if (sample) *sample = s;
+    if (factor) *factor = 1;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_blocks_size(sympix_plan_t pl, int storage, size_t *bytes, int64_t *elements) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_blocks_size: NULL plan");
+    if (storage != SYMPIX_STORE_PBAND && storage != SYMPIX_STORE_DENSE)
+        return set_error(SYMPIX_EINVAL, "sympix_blocks_size: unknown storage %d", storage);
+    const bool pb = storage == SYMPIX_STORE_PBAND;
+    if (bytes) *bytes = (size_t)(pb ? pl->size_pband : pl->size_dense) * sizeof(double);
+    if (elements) *elements = pb ? pl->elems_pband : pl->elems_dense;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_block_layout(sympix_plan_t pl, int storage, int op, int ring, int64_t *offset, int32_t *n,
+                                   int32_t *w, int32_t *format) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_block_layout: NULL plan");
+    if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1)
+        return set_error(SYMPIX_EINVAL, "sympix_block_layout: (op %d, ring %d) not planned", op, ring);
+    const BlockDesc &bd = pl->blocks[(size_t)op * (pl->ring1 - pl->ring0) + (ring - pl->ring0)];
+    const bool pb = storage == SYMPIX_STORE_PBAND;
+    if (offset) *offset = pb ? bd.off_pband : bd.off_dense;
+    if (n) *n = bd.n;
+    if (w) *w = bd.w;
+    if (format) *format = pb ? bd.format : SYMPIX_BLOCK_DENSE;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_support_copy(sympix_plan_t pl, int op, int ring, int radius, int32_t *mmax) {
+    if (!pl || !mmax) return set_error(SYMPIX_EINVAL, "sympix_support_copy: NULL argument");
+    if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1 || radius < 0)
+        return set_error(SYMPIX_EINVAL, "sympix_support_copy: (op %d, ring %d) not planned", op, ring);
+    for (int i = 0; i <= 2 * radius; ++i) mmax[i] = -1;
+    const BlockDesc &bd = pl->blocks[(size_t)op * (pl->ring1 - pl->ring0) + (ring - pl->ring0)];
+    for (int e = 0; e < bd.npairs; ++e) {
+        const PairEntry &pe = pl->entries[bd.pair0 + e];
+        const int d = pe.rho - ring;
+        if (d >= -radius && d <= radius) mmax[d + radius] = pe.mmax;
+    }
+    return SYMPIX_OK;
+}
+
+extern "C" void sympix_plan_free(sympix_plan_t pl) { delete pl; }

@@ -1,0 +1,154 @@
+// Kernel tables: b(x) = sum_{l=0}^{lmax} (2l+1)/(4 pi) b_l P_l(x) (Eq.
+// addition-theorem) and d(x) likewise, at every symmetry-class slot, in FP64.
+//
+// x is carried as u = 1 - x (exact haversine form from the plan).  P_l is
+// advanced on its differences D_l = P_l - P_{l-1}:
+//   D_{l+1} = A_l D_l - B_l u P_l,  P_{l+1} = P_l + D_{l+1},
+//   A_l = l / (l+1),  B_l = (2l+1) / (l+1),
+// the three-term recurrence rearranged for x near 1, where the kernel is
+// steep (d b / d x ~ b / sigma^2) and rounding x itself would cost ~1e-10.
+// Coefficients (A_l, B_l) and the scaled c'_l = (2l+1) c_l / (4 pi) are
+// staged once per launch in global memory and read as warp-uniform loads.
+#include "sympix_internal.cuh"
+
+namespace sympix {
+
+__global__ void k_table_coeffs(int lmax, int nops, const double *__restrict__ bl, const double *__restrict__ dl,
+                               double *__restrict__ rec, double *__restrict__ cb, double *__restrict__ cd) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int L1 = lmax + 1;
+    if (i < L1) {
+        double l = (double)i;
+        rec[2 * i] = l / (l + 1.0);
+        rec[2 * i + 1] = (2.0 * l + 1.0) / (l + 1.0);
+    }
+    if (i < nops * L1) {
+        const double f = (2.0 * (double)(i % L1) + 1.0) / (4.0 * kPi);
+        cb[i] = f * bl[i];
+        cd[i] = f * dl[i];
+    }
+}
+
+// One thread per slot; the same-ring slots also get d.  nops operators are
+// summed from one pass of the recurrence.
+template <int NOPS>
+__global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, int op0, int lmax,
+                                               const double *__restrict__ slot_u,
+                                               const int32_t *__restrict__ slot_pair,
+                                               const CanonPair *__restrict__ pairs,
+                                               const double *__restrict__ rec, const double *__restrict__ cb,
+                                               const double *__restrict__ cd, double *__restrict__ tb,
+                                               double *__restrict__ td, float *__restrict__ tb32,
+                                               float *__restrict__ tblo) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const double u = slot_u[s];
+    const CanonPair cp = pairs[slot_pair[s]];
+    const bool same = cp.a == cp.b;
+    const int L1 = lmax + 1;
+    const int nops = min(NOPS, nops_total - op0);
+    double sb[NOPS], sd[NOPS];
+    double p = 1.0, dlt = -u;
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) {
+        sb[o] = 0.0;
+        sd[o] = 0.0;
+        if (o < nops) {
+            sb[o] = cb[(op0 + o) * L1];
+            if (same) sd[o] = cd[(op0 + o) * L1];
+        }
+    }
+    if (lmax >= 1) {
+        p = 1.0 - u;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o)
+            if (o < nops) {
+                sb[o] = fma(cb[(op0 + o) * L1 + 1], p, sb[o]);
+                if (same) sd[o] = fma(cd[(op0 + o) * L1 + 1], p, sd[o]);
+            }
+    }
+    for (int l = 1; l < lmax; ++l) {
+        const double A = rec[2 * l], B = rec[2 * l + 1];
+        dlt = fma(A, dlt, -B * (u * p));
+        p += dlt;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o)
+            if (o < nops) {
+                sb[o] = fma(cb[(op0 + o) * L1 + l + 1], p, sb[o]);
+                if (same) sd[o] = fma(cd[(op0 + o) * L1 + l + 1], p, sd[o]);
+            }
+    }
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o)
+        if (o < nops) {
+            const int64_t idx = (int64_t)(op0 + o) * nslots + s;
+            tb[idx] = sb[o];
+            td[idx] = same ? sd[o] : 0.0;
+            const float hi = (float)sb[o];
+            tb32[idx] = hi;
+            tblo[idx] = (float)(sb[o] - (double)hi);
+        }
+}
+
+}  // namespace sympix
+
+using namespace sympix;
+
+extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const double *dl, void *stream) {
+    if (!pl || !bl || !dl) return set_error(SYMPIX_EINVAL, "sympix_kernel_table: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int lmax = pl->grid->lmax;
+    const int L1 = lmax + 1;
+    int rc;
+    if (pl->d_rec.n < (size_t)(2 * L1 + 2 * pl->nops * L1)) {
+        if ((rc = pl->d_rec.alloc((size_t)(2 * L1 + 2 * pl->nops * L1)))) return rc;
+    }
+    double *rec = pl->d_rec.p;
+    double *cb = rec + 2 * L1;
+    double *cd = cb + (size_t)pl->nops * L1;
+    const int tot = pl->nops * L1;
+    k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
+    if (pl->nslots > 0) {
+        const unsigned grid = (unsigned)((pl->nslots + 127) / 128);
+        for (int op0 = 0; op0 < pl->nops;) {
+            const int left = pl->nops - op0;
+            const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+#define SPX_TABLE(NO)                                                                                              \
+    k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+                                      pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
+                                      pl->d_tab_blo.p)
+            if (chunk == 4)
+                SPX_TABLE(4);
+            else if (chunk == 2)
+                SPX_TABLE(2);
+            else
+                SPX_TABLE(1);
+#undef SPX_TABLE
+            op0 += chunk;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table: launch");
+    pl->table_ready = true;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_table_copy(sympix_plan_t pl, int op, int ring, int rho, int count, double *b, double *d) {
+    if (!pl || !b) return set_error(SYMPIX_EINVAL, "sympix_table_copy: NULL argument");
+    if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1)
+        return set_error(SYMPIX_EINVAL, "sympix_table_copy: (op %d, ring %d) not planned", op, ring);
+    const BlockDesc &bd = pl->blocks[(size_t)op * (pl->ring1 - pl->ring0) + (ring - pl->ring0)];
+    for (int e = 0; e < bd.npairs; ++e) {
+        const PairEntry &pe = pl->entries[bd.pair0 + e];
+        if (pe.rho != rho) continue;
+        const int K = pe.mmax / 2 + 1;
+        if (count > K) return set_error(SYMPIX_EINVAL, "sympix_table_copy: %d values requested, %d stored", count, K);
+        SPX_CUDA(cudaMemcpy(b, pl->d_tab_b.p + (size_t)op * pl->nslots + pe.tab, count * sizeof(double),
+                            cudaMemcpyDeviceToHost));
+        if (d && rho == ring)
+            SPX_CUDA(cudaMemcpy(d, pl->d_tab_d.p + (size_t)op * pl->nslots + pe.tab, count * sizeof(double),
+                                cudaMemcpyDeviceToHost));
+        return SYMPIX_OK;
+    }
+    return set_error(SYMPIX_EINVAL, "sympix_table_copy: ring %d does not couple to ring %d", rho, ring);
+}

@@ -1,0 +1,282 @@
+"""ctypes binding of libsympix (C ABI in include/sympix.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions keep the C names (``sympix_grid``, ``sympix_support``,
+``sympix_kernel_table``, ``sympix_sample_blocks``, ``sympix_factor_blocks``);
+device buffers are torch CUDA tensors and streams are torch streams.  If the
+library is not built or no GPU is usable the calls raise; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+LAYOUT_GREEDY, LAYOUT_DP = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
+STORE_PBAND, STORE_DENSE = 0, 1
+BLOCK_PBAND, BLOCK_DENSE = 0, 1
+
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp32x2": PREC_FP32X2}
+STORAGES = {"pband": STORE_PBAND, "dense": STORE_DENSE}
+
+
+class SympixError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sympix error {code}: {msg}")
+        self.code = code
+
+
+class _GridDesc(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("k", ctypes.c_int), ("layout", ctypes.c_int),
+                ("nrings", ctypes.c_int), ("nbands", ctypes.c_int), ("max_ring", ctypes.c_int),
+                ("npix", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dp = ctypes.POINTER(ctypes.c_double)
+_sizep = ctypes.POINTER(ctypes.c_size_t)
+
+# (name, restype, argtypes) of every exported symbol declared in sympix.h
+SIGNATURES = [
+    ("sympix_grid", _i, [_i, _i, _i, ctypes.c_double, ctypes.POINTER(_vp)]),
+    ("sympix_grid_describe", _i, [_vp, ctypes.POINTER(_GridDesc)]),
+    ("sympix_grid_copy", _i, [_vp, _dp, _i32p, _i64p, _i32p]),
+    ("sympix_grid_free", None, [_vp]),
+    ("sympix_support", _i, [_vp, _i, _dp, _i, _i, ctypes.POINTER(_vp)]),
+    ("sympix_plan_counts", _i, [_vp, _i64p, _i64p, _i64p, _i64p]),
+    ("sympix_plan_launches", _i, [_vp, _i, _i32p, _i32p, _i32p]),
+    ("sympix_blocks_size", _i, [_vp, _i, _sizep, _i64p]),
+    ("sympix_block_layout", _i, [_vp, _i, _i, _i, _i64p, _i32p, _i32p, _i32p]),
+    ("sympix_support_copy", _i, [_vp, _i, _i, _i, _i32p]),
+    ("sympix_kernel_table", _i, [_vp, _vp, _vp, _vp]),
+    ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
+    ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
+    ("sympix_factor_blocks", _i, [_vp, _i, _vp, _vp, _vp]),
+    ("sympix_plan_free", None, [_vp]),
+    ("sympix_last_error", ctypes.c_char_p, []),
+    ("sympix_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libsympix.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise SympixError(ECUDA, f"{LIB_PATH.name} is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(str(LIB_PATH))
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise SympixError(rc, lib().sympix_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    if not t.is_cuda:
+        raise SympixError(EINVAL, "expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise SympixError(EINVAL, "expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# -- handles ------------------------------------------------------------------------
+
+class Grid:
+    """A SymPix grid (sympix_grid)."""
+
+    def __init__(self, lmax: int, k: int = 1, layout: str = "greedy", polar_thr: float = -1.0):
+        h = _vp()
+        lay = {"greedy": LAYOUT_GREEDY, "dp": LAYOUT_DP}[layout]
+        _check(lib().sympix_grid(int(lmax), int(k), lay, float(polar_thr), ctypes.byref(h)))
+        self._h = h
+        d = _GridDesc()
+        _check(lib().sympix_grid_describe(h, ctypes.byref(d)))
+        self.lmax, self.k, self.nrings, self.nbands = d.lmax, d.k, d.nrings, d.nbands
+        self.max_ring, self.npix = d.max_ring, d.npix
+        N = d.nrings
+        self.theta = np.zeros(N)
+        self.nring = np.zeros(N, np.int32)
+        self.ring_offset = np.zeros(N, np.int64)
+        self.ring_stride = np.zeros(N, np.int32)
+        _check(lib().sympix_grid_copy(h, self.theta.ctypes.data_as(_dp), self.nring.ctypes.data_as(_i32p),
+                                      self.ring_offset.ctypes.data_as(_i64p),
+                                      self.ring_stride.ctypes.data_as(_i32p)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def as_dict(self) -> dict:
+        return dict(lmax=self.lmax, k=self.k, nrings=self.nrings, theta=self.theta, nring=self.nring,
+                    ring_offset=self.ring_offset, ring_stride=self.ring_stride, npix=int(self.npix))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sympix_grid_free(h)
+            self._h = None
+
+
+class Plan:
+    """Support, classes and block layout of nops operators (sympix_support)."""
+
+    def __init__(self, grid: Grid, r_s, ring0: int = 0, ring1: int | None = None):
+        r = np.ascontiguousarray(np.atleast_1d(r_s), dtype=np.float64)
+        self.grid = grid
+        self.nops = len(r)
+        self.ring0 = int(ring0)
+        self.ring1 = grid.nrings if ring1 is None else int(ring1)
+        h = _vp()
+        _check(lib().sympix_support(grid.handle, self.nops, r.ctypes.data_as(_dp), self.ring0, self.ring1,
+                                    ctypes.byref(h)))
+        self._h = h
+        ns, npairs, nt, nm = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().sympix_plan_counts(h, ctypes.byref(ns), ctypes.byref(npairs), ctypes.byref(nt),
+                                        ctypes.byref(nm)))
+        self.nslots, self.npairs, self.ntriples, self.nmults = ns.value, npairs.value, nt.value, nm.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nblocks(self) -> int:
+        return self.nops * (self.ring1 - self.ring0)
+
+    def blocks_size(self, storage="pband"):
+        b, e = ctypes.c_size_t(), ctypes.c_int64()
+        _check(lib().sympix_blocks_size(self._h, STORAGES[storage], ctypes.byref(b), ctypes.byref(e)))
+        return b.value, e.value
+
+    def block_layout(self, storage, op, ring):
+        off, n, w, fmt = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sympix_block_layout(self._h, STORAGES[storage], int(op), int(ring), ctypes.byref(off),
+                                         ctypes.byref(n), ctypes.byref(w), ctypes.byref(fmt)))
+        return off.value, n.value, w.value, fmt.value
+
+    def launches(self, storage="pband"):
+        """Kernel launches of (kernel_table, sample_blocks, factor_blocks)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sympix_plan_launches(self._h, STORAGES[storage], ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def support(self, op, ring, radius):
+        out = np.zeros(2 * radius + 1, np.int32)
+        _check(lib().sympix_support_copy(self._h, int(op), int(ring), int(radius), out.ctypes.data_as(_i32p)))
+        return out
+
+    def table(self, op, ring, rho, count):
+        b = np.zeros(count)
+        d = np.zeros(count)
+        _check(lib().sympix_table_copy(self._h, int(op), int(ring), int(rho), int(count), b.ctypes.data_as(_dp),
+                                       d.ctypes.data_as(_dp) if rho == ring else None))
+        return b, (d if rho == ring else None)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sympix_plan_free(h)
+            self._h = None
+
+
+# -- the C entry points under their own names ----------------------------------------
+
+def sympix_grid(lmax, k=1, layout="greedy", polar_thr=-1.0) -> Grid:
+    return Grid(lmax, k, layout, polar_thr)
+
+
+def sympix_support(grid: Grid, r_s, ring0=0, ring1=None) -> Plan:
+    return Plan(grid, r_s, ring0, ring1)
+
+
+def sympix_kernel_table(plan: Plan, bl, dl, stream=None):
+    """bl, dl: CUDA float64 tensors [nops, lmax+1]."""
+    L1 = plan.grid.lmax + 1
+    for t in (bl, dl):
+        if t.dtype.itemsize != 8 or tuple(t.shape) != (plan.nops, L1):
+            raise SympixError(EINVAL, f"coefficients must be float64 [{plan.nops}, {L1}]")
+    _check(lib().sympix_kernel_table(plan.handle, _ptr(bl), _ptr(dl), _stream(stream)))
+
+
+def sympix_sample_blocks(plan: Plan, ninv, precision="fp64", storage="pband", out=None, stream=None):
+    """ninv: CUDA float64 tensor [nops, npix]; returns the blocks buffer."""
+    import torch
+    if ninv.dtype != torch.float64 or tuple(ninv.shape) != (plan.nops, plan.grid.npix):
+        raise SympixError(EINVAL, f"ninv must be float64 [{plan.nops}, {plan.grid.npix}]")
+    nbytes, _ = plan.blocks_size(storage)
+    if out is None:
+        out = torch.empty(nbytes // 8, dtype=torch.float64, device=ninv.device)
+    elif out.numel() * out.element_size() < nbytes:
+        raise SympixError(EINVAL, "blocks buffer too small")
+    _check(lib().sympix_sample_blocks(plan.handle, _ptr(ninv), PRECISIONS[precision], STORAGES[storage],
+                                      _ptr(out), _stream(stream)))
+    return out
+
+
+def sympix_factor_blocks(plan: Plan, blocks, storage="pband", info=None, stream=None):
+    import torch
+    if info is None:
+        info = torch.empty(plan.nblocks, dtype=torch.int32, device=blocks.device)
+    _check(lib().sympix_factor_blocks(plan.handle, STORAGES[storage], _ptr(blocks), _ptr(info),
+                                      _stream(stream)))
+    return info
+
+
+# -- host-side views of the block buffer (for tests and users) -----------------------
+
+def unpack_block(blocks: np.ndarray, plan: Plan, storage: str, op: int, ring: int,
+                 factored: bool = False) -> np.ndarray:
+    """Dense n x n matrix of one block from a host copy of the blocks buffer:
+    the symmetric M (sampled) or the lower factor L (factored)."""
+    off, n, w, fmt = plan.block_layout(storage, op, ring)
+    if fmt == BLOCK_DENSE:
+        A = blocks[off:off + n * n].reshape(n, n).copy()
+        return np.tril(A) if factored else A
+    band = blocks[off:off + n * (w + 1)].reshape(n, w + 1)
+    M = np.zeros((n, n))
+    q = np.arange(n)
+    if not factored:
+        for d in range(w + 1):
+            r = (q - d) % n
+            M[q, r] = band[:, d]
+            M[r, q] = band[:, d]
+        return M
+    m = n - w
+    for d in range(w + 1):
+        rows = q[(q < m) & (q >= d)]
+        M[rows, rows - d] = band[rows, d]
+    bord = blocks[off + n * (w + 1):off + n * (2 * w + 1)].reshape(w, n)
+    for b in range(w):
+        i = m + b
+        M[i, :i + 1] = bord[b, :i + 1]
+    return M
+
+
+def version() -> str:
+    return lib().sympix_version().decode()

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer outputs (ring counts, pixel numbering, coupled pixel sets, band
+widths) must match bit for bit; floating-point outputs within the stated
+tolerances, normwise per block: max|x - x_ref| / max|x_ref| <= 1e-10 for the
+FP64 and split-FP32 contractions, <= 1e-6 for the FP32 contraction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1504_04653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32x2": 1e-10, "fp32": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1504_04653_gb300 import sympix
+    return sympix
+
+
+@pytest.fixture(scope="module")
+def dev(S):
+    import torch
+    return torch.device("cuda", 0)
+
+
+def _err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _run(S, dev, wl, grid=None, ring0=0, ring1=None, precision="fp64", storage="pband", factor=False,
+         ninv_h=None, radii=None):
+    import torch
+    grid = grid or S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii() if radii is None else radii, ring0, ring1)
+    bl = torch.tensor(wl.beams(), dtype=torch.float64, device=dev)
+    dl = torch.tensor(wl.priors(), dtype=torch.float64, device=dev)
+    if ninv_h is None:
+        colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+        ninv_h = wl.ninv(colat)
+    ninv = torch.tensor(ninv_h, dtype=torch.float64, device=dev)
+    S.sympix_kernel_table(plan, bl, dl)
+    blocks = S.sympix_sample_blocks(plan, ninv, precision=precision, storage=storage)
+    sampled = blocks.cpu().numpy()
+    out = dict(grid=grid, plan=plan, sampled=sampled, ninv=ninv_h)
+    if factor:
+        info = S.sympix_factor_blocks(plan, blocks, storage=storage)
+        out["info"] = info.cpu().numpy()
+        out["factored"] = blocks.cpu().numpy()
+    return out
+
+
+# -- grid --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lmax", [1, 2, 7, 64, 65, 500, 1000, 3000])
+def test_greedy_grid_matches_oracle(S, lmax):
+    g = S.Grid(lmax)
+    og = O.grid(lmax)
+    assert np.array_equal(g.nring, og["nring"])
+    assert np.array_equal(g.ring_offset, og["ring_offset"])
+    assert np.array_equal(g.ring_stride, og["ring_stride"])
+    assert g.npix == og["npix"]
+    assert np.max(np.abs(g.theta - og["theta"]) / og["theta"]) <= 4e-15
+
+
+@pytest.mark.parametrize("lmax,k,thr", [(767, 8, 0.0), (511, 8, 0.0), (2000, 4, 0.0), (511, 8, -1.0),
+                                        (63, 2, 0.0), (100, 1, 5.0)])
+def test_dp_grid_matches_oracle(S, lmax, k, thr):
+    g = S.Grid(lmax, k=k, layout="dp", polar_thr=thr)
+    og = O.grid(lmax, k=k, layout="dp", thr=thr)
+    assert np.array_equal(g.nring, og["nring"])
+    assert np.array_equal(g.ring_offset, og["ring_offset"])
+    assert np.array_equal(g.ring_stride, og["ring_stride"])
+    if (lmax, k, thr) == (767, 8, 0.0):
+        assert g.npix == 838656  # Table comparison
+
+
+# -- support and kernel table ---------------------------------------------------------
+
+def _coupled_from_mmax(n_j, n_rho, c, m):
+    g = math.gcd(n_j, n_rho)
+    P, Q = n_j // g, n_rho // g
+    half = P * n_rho
+    out = []
+    for p in range(n_rho):
+        z = ((2 * c + 1) * Q - (2 * p + 1) * P) % (2 * half)
+        if z > half:
+            z -= 2 * half
+        if abs(z) <= m:
+            out.append(p)
+    return np.array(out, dtype=np.int32)
+
+
+@pytest.mark.parametrize("name,rings", [("lmax64", None), ("lmax500", [0, 1, 2, 3, 60, 249, 250, 251, 498, 500])])
+def test_support_matches_oracle_bruteforce(S, name, rings):
+    wl = W.WORKLOADS[name]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    og = O.grid(wl.lmax)
+    r_s = wl.radii()[0]
+    N = grid.nrings
+    R = 12
+    for j in (rings if rings is not None else range(N)):
+        mm = plan.support(0, j, R)
+        for d in range(-R, R + 1):
+            rho = j + d
+            if rho < 0 or rho >= N:
+                continue
+            n_j, n_r = int(grid.nring[j]), int(grid.nring[rho])
+            for c in sorted({0, 1, n_j // 3, n_j - 1}):
+                ref = O.coupled(og, j, c, rho, r_s)
+                got = _coupled_from_mmax(n_j, n_r, c, mm[d + R]) if mm[d + R] >= 0 else np.zeros(0, np.int32)
+                assert np.array_equal(got, ref), (j, rho, c)
+
+
+@pytest.mark.parametrize("name", ["lmax64", "lmax500", "lmax3000"])
+def test_kernel_table_matches_oracle(S, dev, name):
+    import torch
+    wl = W.WORKLOADS[name]
+    grid = S.Grid(wl.lmax)
+    N = grid.nrings
+    rings = [0, 1, N // 4, N // 2, N - 1]
+    plan = S.Plan(grid, wl.radii())
+    og = O.grid(wl.lmax)
+    bl, dl = wl.beams()[0], wl.priors()[0]
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    torch.cuda.synchronize()
+    peak_b = O.kernel_u(wl.lmax, bl, 0.0)[0]
+    peak_d = O.kernel_u(wl.lmax, dl, 0.0)[0]
+    R = 8
+    for j in rings:
+        mm = plan.support(0, j, R)
+        for d in range(-R, R + 1):
+            m = mm[d + R]
+            if m < 0:
+                continue
+            rho = j + d
+            n_j, n_r = int(grid.nring[j]), int(grid.nring[rho])
+            g = math.gcd(n_j, n_r)
+            P, Q = n_j // g, n_r // g
+            K = m // 2 + 1
+            b, dd = plan.table(0, j, rho, K)
+            # one representative pixel pair per class: c = 0, p with |z| = level
+            for k in range(0, K, max(1, K // 4)):
+                lev = (m % 2) + 2 * k
+                found = None
+                for c in range(P):
+                    for p in range(-n_r, 2 * n_r):
+                        if abs((2 * c + 1) * Q - (2 * p + 1) * P) == lev:
+                            found = (c, p % n_r)
+                            break
+                    if found:
+                        break
+                assert found is not None
+                u = O.pair_u(og["theta"][j], n_j, found[0], og["theta"][rho], n_r, found[1])
+                ref = O.kernel_u(wl.lmax, bl, u)[0]
+                assert abs(b[k] - ref) <= 1e-10 * peak_b, (j, rho, k)
+                if rho == j:
+                    refd = O.kernel_u(wl.lmax, dl, u)[0]
+                    assert abs(dd[k] - refd) <= 1e-10 * peak_d
+
+
+# -- blocks ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32x2"])
+@pytest.mark.parametrize("storage", ["pband", "dense"])
+def test_blocks_lmax64_all(S, dev, precision, storage):
+    wl = W.WORKLOADS["lmax64"]
+    r = _run(S, dev, wl, precision=precision, storage=storage, factor=True)
+    og = O.grid(wl.lmax)
+    plan = r["plan"]
+    assert np.all(r["info"] == 0)
+    for j in range(og["nrings"]):
+        M = S.unpack_block(r["sampled"], plan, storage, 0, j)
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], r["ninv"][0], j)
+        assert _err(M, ref) <= TOL[precision], (j, _err(M, ref))
+        L = S.unpack_block(r["factored"], plan, storage, 0, j, factored=True)
+        Lref, info = O.cholesky(ref)
+        assert info == 0
+        assert _err(L, Lref) <= 50 * TOL[precision], (j, _err(L, Lref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32x2"])
+def test_blocks_lmax500_sampled(S, dev, precision):
+    wl = W.WORKLOADS["lmax500"]
+    r = _run(S, dev, wl, precision=precision, factor=True)
+    og = O.grid(wl.lmax)
+    plan = r["plan"]
+    assert np.all(r["info"] == 0)
+    for j in (0, 1, 2, 77, 249, 250, 251, 423, 500):
+        M = S.unpack_block(r["sampled"], plan, "pband", 0, j)
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], r["ninv"][0], j)
+        assert _err(M, ref) <= TOL[precision], (j, _err(M, ref))
+        L = S.unpack_block(r["factored"], plan, "pband", 0, j, factored=True)
+        # the factor reproduces the oracle's block
+        assert _err(L @ L.T, ref) <= 10 * TOL[precision], j
+        if M.shape[0] <= 300:
+            Lref, _ = O.cholesky(ref)
+            assert _err(L, Lref) <= 100 * TOL[precision], j
+
+
+def test_block_widths_match_oracle_structure(S, dev):
+    """The stored band covers exactly the oracle's structural nonzeros."""
+    wl = W.WORKLOADS["lmax64"]
+    r = _run(S, dev, wl)
+    og = O.grid(wl.lmax)
+    rng = np.random.default_rng(9)
+    ninv = rng.uniform(0.5, 2.0, og["npix"])  # no masked zeros: structure = support
+    for j in (10, 20, 32, 50):
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv, j)
+        _, n, w, fmt = r["plan"].block_layout("pband", 0, j)
+        if fmt != 0:
+            continue
+        q = np.arange(n)
+        dist = np.minimum((q[:, None] - q[None, :]) % n, (q[None, :] - q[:, None]) % n)
+        assert np.all(ref[dist > w] == 0.0)
+        assert np.any(ref[dist == w] != 0.0)
+
+
+def test_ring_range_and_batched_operators(S, dev):
+    """A ring sub-range, and several operators in one plan, reproduce the
+    single-operator full plan block by block."""
+    import torch
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(wl.lmax)
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    multi = W.Workload("multi", 64, [180.0, 120.0, 240.0], [20.0, 0.0, 30.0], [1, 7, 8])
+    full = _run(S, dev, multi, grid=grid, precision="fp64", factor=True)
+    sub = _run(S, dev, multi, grid=grid, ring0=20, ring1=33, precision="fp64", factor=True)
+    og = O.grid(64)
+    ninv_h = multi.ninv(colat)
+    for o in range(3):
+        for j in (20, 26, 32):
+            A = S.unpack_block(full["sampled"], full["plan"], "pband", o, j)
+            B = S.unpack_block(sub["sampled"], sub["plan"], "pband", o, j)
+            assert np.array_equal(A, B)
+            ref, _ = O.block(og, multi.beams()[o], multi.priors()[o], multi.radii()[o], ninv_h[o], j)
+            assert _err(A, ref) <= 1e-10
+            # a truncated prior over a masked ring need not be definite: the
+            # pivot report must agree with the oracle's Cholesky
+            _, info = O.cholesky(ref)
+            assert full["info"][o * 65 + j] == info
+            assert sub["info"][o * 13 + (j - 20)] == info
+
+
+def test_no_truncation_and_tiny_grids(S, dev):
+    """r_s >= pi couples every pixel pair (dense blocks), l_max = 1 and 6."""
+    for lmax in (1, 6):
+        wl = W.Workload("tiny", lmax, [600.0], [0.0], [3])
+        r = _run(S, dev, wl, radii=np.array([math.pi]), precision="fp64", factor=True)
+        og = O.grid(lmax)
+        for j in range(og["nrings"]):
+            M = S.unpack_block(r["sampled"], r["plan"], "pband", 0, j)
+            ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], math.pi, r["ninv"][0], j)
+            assert _err(M, ref) <= 1e-10
+
+
+def test_masked_everywhere_gives_prior_only(S, dev):
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(64)
+    r = _run(S, dev, wl, grid=grid, ninv_h=np.zeros((1, grid.npix)), precision="fp32")
+    og = O.grid(64)
+    for j in (0, 32):
+        M = S.unpack_block(r["sampled"], r["plan"], "pband", 0, j)
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], np.zeros(grid.npix), j)
+        assert _err(M, ref) <= 1e-12
+
+
+def test_indefinite_block_reports_pivot(S, dev):
+    """A negative inverse-noise value makes blocks indefinite: info names the
+    first bad pivot exactly as the oracle's Cholesky does."""
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(64)
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    ninv = wl.ninv(colat)
+    ninv[0, : grid.npix // 3] *= -40.0
+    r = _run(S, dev, wl, grid=grid, ninv_h=ninv, precision="fp64", factor=True)
+    og = O.grid(64)
+    bad = 0
+    for j in range(og["nrings"]):
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv[0], j)
+        _, info = O.cholesky(ref)
+        assert r["info"][j] == info, j
+        bad += info > 0
+    assert bad > 0
+
+
+# -- full size, in the bench's configuration ----------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32x2", "fp64"])
+def test_full_size_lmax3000_sampled(S, dev, precision):
+    """l_max = 3000, FWHM 5': every block factors; sampled blocks match the
+    oracle and their factors reproduce them."""
+    wl = W.WORKLOADS["lmax3000"]
+    r = _run(S, dev, wl, precision=precision, factor=True)
+    assert np.all(r["info"] == 0)
+    og = O.grid(wl.lmax)
+    plan = r["plan"]
+    for j in (0, 2, 37, 1500 if precision == "fp32" else 250):
+        M = S.unpack_block(r["sampled"], plan, "pband", 0, j)
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], r["ninv"][0], j)
+        assert _err(M, ref) <= TOL[precision], (j, _err(M, ref))
+        L = S.unpack_block(r["factored"], plan, "pband", 0, j, factored=True)
+        assert _err(L @ L.T, ref) <= 10 * TOL[precision], j
