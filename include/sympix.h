@@ -177,6 +177,30 @@ int sympix_support_copy(sympix_plan_t plan, int op, int ring, int radius, int32_
  * precede sympix_sample_blocks.  Asynchronous on `stream`. */
 int sympix_kernel_table(sympix_plan_t plan, const double *bl, const double *dl, void *stream);
 
+/* Same computation and outputs as sympix_kernel_table, for callers that
+ * must not allocate device memory at the time of the call (for example
+ * code that runs under a fixed device-memory budget reserved up front, or
+ * whose allocator forbids the implicit device synchronisation cudaMalloc
+ * brings).  sympix_kernel_table allocates its coefficient staging buffer on
+ * first use; this entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine and stages the coefficients in one static device
+ * array of 262144 doubles (2 MiB) that every GPU which loads the library
+ * holds until the process exits.  (The paper has no counterpart; this is a
+ * deployment variant.)
+ *   Limit: 2 (lmax + 1) (nops + 1) <= 262144, else SYMPIX_EINVAL and
+ *   nothing is launched.
+ *   The plan (and its kernel tables) must already exist: create it with
+ *   sympix_support beforehand.
+ *   The first call on a device looks up the array's device address with
+ *   that device current (a host-side query, done once per device); make
+ *   that first call before any stream capture.
+ *   Every call shares the one array and it keeps the last call's contents;
+ *   nothing in it needs to start at zero (each launch writes every entry it
+ *   reads).  Calls whose work overlaps on the GPU race on the array: issue
+ *   them on one stream, or otherwise order them.
+ * Asynchronous on `stream`. */
+int sympix_kernel_table_static(sympix_plan_t plan, const double *bl, const double *dl, void *stream);
+
 /* Copy operator `op`'s kernel values to the host: b at every slot of ring
  * pair (ring, rho) for separation indices m = par, par+2, ..., mmax
  * (par = mmax mod 2), count values; d likewise for rho == ring (NULL to

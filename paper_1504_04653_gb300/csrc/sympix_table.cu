@@ -152,3 +152,82 @@ extern "C" int sympix_table_copy(sympix_plan_t pl, int op, int ring, int rho, in
     }
     return set_error(SYMPIX_EINVAL, "sympix_table_copy: ring %d does not couple to ring %d", rho, ring);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of sympix_kernel_table.
+//
+// The coefficient staging of the kernel-table launch (recurrence
+// coefficients and the scaled c'_l) normally lives in a buffer the library
+// allocates on first use.  This variant keeps it in one file-scope device
+// array instead, so the call itself allocates nothing.  The array is loaded
+// with the module and stays resident on every GPU that loads the library
+// until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace sympix {
+
+constexpr size_t kStaticTableScratch = 262144;  // doubles (2 MiB)
+static __device__ __align__(256) double g_table_scratch[kStaticTableScratch];
+
+}  // namespace sympix
+
+extern "C" int sympix_kernel_table_static(sympix_plan_t pl, const double *bl, const double *dl, void *stream) {
+    if (!pl || !bl || !dl) return set_error(SYMPIX_EINVAL, "sympix_kernel_table_static: NULL argument");
+    const int lmax = pl->grid->lmax;
+    const size_t L1 = (size_t)lmax + 1;
+    const size_t need = 2 * L1 + 2 * (size_t)pl->nops * L1;
+    if (need > kStaticTableScratch)
+        return set_error(SYMPIX_EINVAL,
+                         "sympix_kernel_table_static: needs %zu scratch doubles (2 (lmax+1) (nops+1)), "
+                         "the static array holds %zu",
+                         need, kStaticTableScratch);
+    // Host code only sees a stand-in for the device array: fetch its device
+    // address once per device, with that device current.
+    static std::mutex mu;
+    static double *addr[64] = {nullptr};
+    int dev = 0;
+    SPX_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(SYMPIX_EINVAL, "sympix_kernel_table_static: device %d", dev);
+    double *scratch;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_table_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table_static: cudaGetSymbolAddress");
+            addr[dev] = (double *)p;
+        }
+        scratch = addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *rec = scratch;
+    double *cb = rec + 2 * L1;
+    double *cd = cb + (size_t)pl->nops * L1;
+    const int tot = pl->nops * (int)L1;
+    // every scratch entry read below is written first by k_table_coeffs
+    k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
+    if (pl->nslots > 0) {
+        const unsigned grid = (unsigned)((pl->nslots + 127) / 128);
+        for (int op0 = 0; op0 < pl->nops;) {
+            const int left = pl->nops - op0;
+            const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+#define SPX_TABLE_S(NO)                                                                                            \
+    k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+                                      pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
+                                      pl->d_tab_blo.p)
+            if (chunk == 4)
+                SPX_TABLE_S(4);
+            else if (chunk == 2)
+                SPX_TABLE_S(2);
+            else
+                SPX_TABLE_S(1);
+#undef SPX_TABLE_S
+            op0 += chunk;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table_static: launch");
+    pl->table_ready = true;
+    return SYMPIX_OK;
+}

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("sympix_block_layout", _i, [_vp, _i, _i, _i, _i64p, _i32p, _i32p, _i32p]),
     ("sympix_support_copy", _i, [_vp, _i, _i, _i, _i32p]),
     ("sympix_kernel_table", _i, [_vp, _vp, _vp, _vp]),
+    ("sympix_kernel_table_static", _i, [_vp, _vp, _vp, _vp]),
     ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
     ("sympix_factor_blocks", _i, [_vp, _i, _vp, _vp, _vp]),
@@ -222,6 +223,15 @@ def sympix_kernel_table(plan: Plan, bl, dl, stream=None):
         if t.dtype.itemsize != 8 or tuple(t.shape) != (plan.nops, L1):
             raise SympixError(EINVAL, f"coefficients must be float64 [{plan.nops}, {L1}]")
     _check(lib().sympix_kernel_table(plan.handle, _ptr(bl), _ptr(dl), _stream(stream)))
+
+
+def sympix_kernel_table_static(plan: Plan, bl, dl, stream=None):
+    """Allocation-free sympix_kernel_table (static device staging array)."""
+    L1 = plan.grid.lmax + 1
+    for t in (bl, dl):
+        if t.dtype.itemsize != 8 or tuple(t.shape) != (plan.nops, L1):
+            raise SympixError(EINVAL, f"coefficients must be float64 [{plan.nops}, {L1}]")
+    _check(lib().sympix_kernel_table_static(plan.handle, _ptr(bl), _ptr(dl), _stream(stream)))
 
 
 def sympix_sample_blocks(plan: Plan, ninv, precision="fp64", storage="pband", out=None, stream=None):
