@@ -43,10 +43,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lmax3000")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32x2", "fp64"])
+    ap.add_argument("--precision", default="fp32:fp32x2",
+                    help="headline arithmetic as contraction:factor (fp64, fp32x2 or fp32 each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--arms", default="fp64,fp32x2", help="extra contraction arms timed beside the headline")
+    ap.add_argument("--arms", default="fp64:fp64,fp32x2:fp32x2,fp32:fp32",
+                    help="other contraction:factor arithmetics timed beside the headline")
     return ap.parse_args()
 
 
@@ -191,15 +193,16 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     def step(prec, ev=None):
+        sprec, fprec = prec.split(":")
         if ev:
             ev[0].record(stream)
         S.sympix_kernel_table(plan, bl, dl, stream=stream)
         if ev:
             ev[1].record(stream)
-        S.sympix_sample_blocks(plan, ninv, precision=prec, storage="pband", out=blocks, stream=stream)
+        S.sympix_sample_blocks(plan, ninv, precision=sprec, storage="pband", out=blocks, stream=stream)
         if ev:
             ev[2].record(stream)
-        S.sympix_factor_blocks(plan, blocks, storage="pband", info=info, stream=stream)
+        S.sympix_factor_blocks(plan, blocks, storage="pband", precision=fprec, info=info, stream=stream)
         if ev:
             ev[3].record(stream)
 
@@ -245,29 +248,36 @@ def main():
         arms[prec] = {"value": elements / (float(st.sum(axis=1).mean()) * 1e-3),
                       "ms_per_step": float(st.sum(axis=1).mean()),
                       "stages_ms": dict(zip(["table", "sample", "factor"], st.mean(axis=0).round(4).tolist()))}
-    # accuracy of the sampled blocks against the FP64 GPU path, normwise per block
+    # accuracy against the FP64 GPU path, normwise per block: sampled blocks
+    # of each contraction, and the factors of each full arm
     acc = {}
     if rank == 0:
-        outs = {}
-        for prec in ("fp64", args.precision, "fp32x2"):
+        offs = [plan.block_layout("pband", 0, j) for j in range(plan.ring0, plan.ring1)]
+        lens = [(off, n * (2 * w + 1) if fmt == 0 else n * n) for off, n, w, fmt in offs]
+
+        def run_once(prec, factored):
+            sprec, fprec = prec.split(":")
             with torch.cuda.stream(stream):
                 S.sympix_kernel_table(plan, bl, dl, stream=stream)
-                S.sympix_sample_blocks(plan, ninv, precision=prec, storage="pband", out=blocks, stream=stream)
+                S.sympix_sample_blocks(plan, ninv, precision=sprec, storage="pband", out=blocks, stream=stream)
+                if factored:
+                    S.sympix_factor_blocks(plan, blocks, storage="pband", precision=fprec, info=info, stream=stream)
             torch.cuda.synchronize()
-            outs[prec] = blocks.clone()
-        offs = [plan.block_layout("pband", 0, j) for j in range(plan.ring0, plan.ring1)]
-        for prec in (args.precision, "fp32x2"):
-            if prec == "fp64":
-                continue
-            worst = 0.0
-            for off, n, w, fmt in offs:
-                ln = n * (w + 1) if fmt == 0 else n * n
-                a = outs[prec][off:off + ln]
-                b = outs["fp64"][off:off + ln]
-                e = float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
-                worst = max(worst, e)
-            acc[f"{prec}_vs_fp64_normwise_max"] = worst
-        del outs
+            return blocks.clone()
+
+        def worst(a, b):
+            e = 0.0
+            for off, ln in lens:
+                x, y = a[off:off + ln], b[off:off + ln]
+                e = max(e, float((x - y).abs().max() / y.abs().max().clamp_min(1e-300)))
+            return e
+
+        for factored in (False, True):
+            ref = run_once("fp64:fp64", factored)
+            for prec in sorted({args.precision, *[a for a in args.arms.split(",") if a]} - {"fp64:fp64"}):
+                key = f"{prec}_{'factor' if factored else 'blocks'}_vs_fp64_normwise_max"
+                acc[key] = worst(run_once(prec, factored), ref)
+            del ref
 
     # e2e: the same step through the public API with host buffers
     e2e = None
@@ -338,7 +348,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 contraction, f64 kernel table and Cholesky",
+        "vs_baseline": None,
+        "dtype": {"fp32:fp32x2": "f64 kernel table, f32 contraction, split-f32 Cholesky",
+                  "fp64:fp64": "f64"}.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": wl.name, "lmax": wl.lmax, "fwhm_arcmin": wl.fwhm_arcmin[0], "nops": plan.nops,
                    "npix": int(grid.npix), "elements": int(elements), "storage": "pband",

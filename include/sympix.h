@@ -223,12 +223,16 @@ int sympix_table_copy(sympix_plan_t plan, int op, int ring, int rho, int count, 
 int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, int storage,
                          double *blocks, void *stream);
 
-/* Cholesky-factor every sampled block in place, M = L L^T, in FP64.
- *   info  device int32 [nops * nblocks] (operator-major, blocks in ring
- *         order): 0, or i+1 for the first row i whose pivot is not positive
- *         (that block's factor is then incomplete).
+/* Cholesky-factor every sampled block in place, M = L L^T.
+ *   precision  arithmetic of the periodic-band factorisation:
+ *              SYMPIX_PREC_FP64, SYMPIX_PREC_FP32X2 (split FP32, near-FP64
+ *              accuracy on the FP32 pipes) or SYMPIX_PREC_FP32.  Dense-format
+ *              blocks and bands wider than 16 are factored in FP64 always.
+ *   info       device int32 [nops * nblocks] (operator-major, blocks in ring
+ *              order): 0, or i+1 for the first row i whose pivot is not
+ *              positive (that block's factor is then incomplete).
  * Asynchronous. */
-int sympix_factor_blocks(sympix_plan_t plan, int storage, double *blocks, int32_t *info,
+int sympix_factor_blocks(sympix_plan_t plan, int storage, int precision, double *blocks, int32_t *info,
                          void *stream);
 
 void sympix_plan_free(sympix_plan_t plan);

@@ -128,7 +128,9 @@ struct sympix_plan_s {
     // sampling schedule (built once)
     std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
     std::vector<SampleItem> items_dense;
-    std::vector<int32_t> factor_order;       // blocks sorted by factor cost
+    // factorisation work lists, each most expensive first: [0] band w <= 8,
+    // [1] band 8 < w <= 16, [2] dense format n <= 1024, [3] everything else
+    std::vector<int32_t> factor_items[4];
     // device
     sympix::DevBuf<CanonPair> d_pairs;
     sympix::DevBuf<double> d_slot_u;         // u = 1 - cos(gamma) per slot
@@ -136,11 +138,13 @@ struct sympix_plan_s {
     sympix::DevBuf<double> d_tab_b, d_tab_d; // [op][nslots] FP64
     sympix::DevBuf<float> d_tab_b32;         // [op][nslots] FP32 (rounded)
     sympix::DevBuf<float> d_tab_blo;         // [op][nslots] FP32 remainder b - hi
+    sympix::DevBuf<float> d_tab_d32, d_tab_dlo; // the same split of d
+    sympix::DevBuf<float> d_ninv32, d_ninvlo;   // [op][npix] split of N^-1, per sampling call
     sympix::DevBuf<double> d_rec;            // recurrence coefficients
     sympix::DevBuf<BlockDesc> d_blocks;
     sympix::DevBuf<PairEntry> d_entries;
     sympix::DevBuf<SampleItem> d_items_pband[5];
     sympix::DevBuf<SampleItem> d_items_dense;
-    sympix::DevBuf<int32_t> d_factor_order;
+    sympix::DevBuf<int32_t> d_factor_items[4];
     bool table_ready = false;
 };

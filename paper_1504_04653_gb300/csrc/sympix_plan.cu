@@ -321,25 +321,37 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             for (int64_t e0 = 0; e0 < ne; e0 += 256) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
         }
     }
-    // factorisation order: most expensive blocks first
-    pl->factor_order.resize(pl->blocks.size());
-    std::iota(pl->factor_order.begin(), pl->factor_order.end(), 0);
+    // factorisation work lists, most expensive blocks first
+    std::vector<int32_t> order(pl->blocks.size());
+    std::iota(order.begin(), order.end(), 0);
     auto cost = [&](int b) {
         const BlockDesc &bd = pl->blocks[b];
         double n = bd.n, w = bd.w;
         return bd.format == SYMPIX_BLOCK_PBAND ? n * (w + 1) * (3 * w + 1) : n * n * n / 3.0;
     };
-    std::stable_sort(pl->factor_order.begin(), pl->factor_order.end(),
-                     [&](int x, int y) { return cost(x) > cost(y); });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    for (int b : order) {
+        const BlockDesc &bd = pl->blocks[b];
+        int list;
+        if (bd.format == SYMPIX_BLOCK_PBAND)
+            list = bd.w <= 8 ? 0 : bd.w <= 16 ? 1 : 3;
+        else
+            list = bd.n <= 1024 ? 2 : 3;
+        pl->factor_items[list].push_back(b);
+    }
 
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
-        (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_factor_order.upload(pl->factor_order)))
+        (rc = pl->d_items_dense.upload(pl->items_dense)))
         return fail(rc);
     for (int bkt = 0; bkt < 5; ++bkt)
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
+    for (int l = 0; l < 4; ++l)
+        if ((rc = pl->d_factor_items[l].upload(pl->factor_items[l]))) return fail(rc);
     const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
+    const size_t nn = (size_t)nops * grid->npix;
     if ((rc = pl->d_tab_b.alloc(tabn)) || (rc = pl->d_tab_d.alloc(tabn)) || (rc = pl->d_tab_b32.alloc(tabn)) ||
-        (rc = pl->d_tab_blo.alloc(tabn)))
+        (rc = pl->d_tab_blo.alloc(tabn)) || (rc = pl->d_tab_d32.alloc(tabn)) || (rc = pl->d_tab_dlo.alloc(tabn)) ||
+        (rc = pl->d_ninv32.alloc(nn)) || (rc = pl->d_ninvlo.alloc(nn)))
         return fail(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(cuda_error(e, "sympix_support"));
@@ -363,10 +375,13 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int32_t *tabl
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_launches: NULL plan");
     if (table) *table = pl->nslots > 0 ? 1 + (pl->nops + 3) / 4 : 1;
     int s = storage == SYMPIX_STORE_DENSE ? 1 : 0;  // the zero fill
+    s += 1;                                          // the N^-1 split (FP32 arithmetics)
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
     if (sample) *sample = s;
-    if (factor) *factor = 1;
+    int f = 0;
+    for (int l = 0; l < 4; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    if (factor) *factor = f;
     return SYMPIX_OK;
 }
 

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
                                                const double *__restrict__ rec, const double *__restrict__ cb,
                                                const double *__restrict__ cd, double *__restrict__ tb,
                                                double *__restrict__ td, float *__restrict__ tb32,
-                                               float *__restrict__ tblo) {
+                                               float *__restrict__ tblo, float *__restrict__ td32,
+                                               float *__restrict__ tdlo) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslots) return;
     const double u = slot_u[s];
@@ -87,6 +88,10 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
             const float hi = (float)sb[o];
             tb32[idx] = hi;
             tblo[idx] = (float)(sb[o] - (double)hi);
+            const double dv = same ? sd[o] : 0.0;
+            const float dh = (float)dv;
+            td32[idx] = dh;
+            tdlo[idx] = (float)(dv - (double)dh);
         }
 }
 
@@ -116,7 +121,7 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
 #define SPX_TABLE(NO)                                                                                              \
     k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
-                                      pl->d_tab_blo.p)
+                                      pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)
                 SPX_TABLE(4);
             else if (chunk == 2)
@@ -215,7 +220,7 @@ extern "C" int sympix_kernel_table_static(sympix_plan_t pl, const double *bl, co
 #define SPX_TABLE_S(NO)                                                                                            \
     k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
-                                      pl->d_tab_blo.p)
+                                      pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)
                 SPX_TABLE_S(4);
             else if (chunk == 2)

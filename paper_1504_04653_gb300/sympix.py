@@ -61,7 +61,7 @@ SIGNATURES = [
     ("sympix_kernel_table_static", _i, [_vp, _vp, _vp, _vp]),
     ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
-    ("sympix_factor_blocks", _i, [_vp, _i, _vp, _vp, _vp]),
+    ("sympix_factor_blocks", _i, [_vp, _i, _i, _vp, _vp, _vp]),
     ("sympix_plan_free", None, [_vp]),
     ("sympix_last_error", ctypes.c_char_p, []),
     ("sympix_version", ctypes.c_char_p, []),
@@ -249,12 +249,12 @@ def sympix_sample_blocks(plan: Plan, ninv, precision="fp64", storage="pband", ou
     return out
 
 
-def sympix_factor_blocks(plan: Plan, blocks, storage="pband", info=None, stream=None):
+def sympix_factor_blocks(plan: Plan, blocks, storage="pband", precision="fp64", info=None, stream=None):
     import torch
     if info is None:
         info = torch.empty(plan.nblocks, dtype=torch.int32, device=blocks.device)
-    _check(lib().sympix_factor_blocks(plan.handle, STORAGES[storage], _ptr(blocks), _ptr(info),
-                                      _stream(stream)))
+    _check(lib().sympix_factor_blocks(plan.handle, STORAGES[storage], PRECISIONS[precision], _ptr(blocks),
+                                      _ptr(info), _stream(stream)))
     return info
 
 

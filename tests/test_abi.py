@@ -45,7 +45,7 @@ def test_argument_errors_need_no_device(lib):
     assert lib.sympix_grid(64, 1, 7, -1.0, ctypes.byref(h)) == S.EINVAL
     assert lib.sympix_support(None, 1, None, 0, 1, ctypes.byref(h)) == S.EINVAL
     assert lib.sympix_sample_blocks(None, None, 0, 0, None, None) == S.EINVAL
-    assert lib.sympix_factor_blocks(None, 0, None, None, None) == S.EINVAL
+    assert lib.sympix_factor_blocks(None, 0, 0, None, None, None) == S.EINVAL
     assert lib.sympix_version().startswith(b"sympix")
 
 
