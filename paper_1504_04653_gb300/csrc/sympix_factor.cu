@@ -266,149 +266,576 @@ __global__ void __launch_bounds__(128) k_factor_band(int nitems, const int32_t *
     if (t == 0) info[bi] = inf;
 }
 
-// One lane per periodic-band block with w <= WB, 32 blocks per warp (the
-// blocks of a warp are adjacent in the plan's cost order, so the lanes run
-// in step).  Everything the elimination of column k touches stays in the
-// lane's registers:
-//   W[r][c]  band rows k..k+w at columns k..k+r (r = 0 is the pivot row);
-//   B[b][c]  border rows m+b at columns k..k+w;
-//   S[b][c]  the corner A22 - L21 L21^T, accumulated as the border rows'
-//            column-k entries of L are produced.
-// Per column: 1/sqrt of the pivot, scale the column, rank-1 update of the
-// band and border windows and of S, shift both windows by one column; the
-// band row entering the window is loaded two columns ahead.  After the last
-// column the w x w corner S is factored in registers.
-template <class A, int WB, bool DENSE>
-__global__ void __launch_bounds__(32) k_factor_lane(int nitems, const int32_t *__restrict__ items,
-                                                    const BlockDesc *__restrict__ blocks, double *__restrict__ out,
-                                                    int32_t *__restrict__ info) {
-    typedef typename A::V V;
-    const int idx = blockIdx.x * 32 + threadIdx.x;
-    if (idx >= nitems) return;
-    const int bi = items[idx];
-    const BlockDesc bd = blocks[bi];
-    const typename ViewOf<DENSE>::T v = ViewOf<DENSE>::make(out, bd);
-    const int w = bd.w, m = bd.n - bd.w;
+// ---------------------------------------------------------------------------
+// Two-pass factorisation of periodic-band blocks.
+//
+// Pass 1 (band): one lane per block factors the band part A11 = L11 L11^T.
+// The lane keeps the active (w+1) x (w+1) triangle W[r][c] (rows k..k+w,
+// columns k..k+r) in registers; per column k it forms 1/sqrt(pivot),
+// scales column k, applies the rank-1 update and shifts the window, the
+// band row entering the window having been loaded two columns ahead.
+// Pass 2 (border): one lane per border row, G2 lanes per block, runs the
+// forward substitution L21 = A21 L11^-T along the band, the band row of L11
+// broadcast by shuffles, and accumulates the corner S = A22 - L21 L21^T on
+// the fly; the w x w corner is then factored by one lane.
+// ---------------------------------------------------------------------------
 
+constexpr int kChunk = 16;  // band rows per staged chunk
+
+// Band pass for one block in one lane.  `stage` (pband storage only) is
+// this lane's shared-memory area of 2 x kChunk x (w+1) doubles: band rows
+// are copied into it a chunk ahead with cp.async, so no global load sits on
+// the elimination chain.  DENSE storage reads rows from global directly.
+template <class A, int WB, class View, bool STAGED>
+__device__ __forceinline__ int band_pass(const View &v, double *stage) {
+    typedef typename A::V V;
+    const int w = v.w, m = v.m, RL = w + 1;
+    auto issue = [&](int j) {
+        if (STAGED) {
+            const int r0 = j * kChunk;
+            if (r0 < m) {
+                const int cnt = min(kChunk, m - r0) * RL;
+                double *dst = stage + (j & 1) * kChunk * RL;
+                const double *src = v.row_elem(r0, w);  // element 0 of row r0
+                for (int i = 0; i < cnt; ++i) cp_async8(dst + i, src + i);
+            }
+            cp_async_commit();
+        }
+    };
+    // A[R][R - w + c] of a band row R < m (entering the window)
+    auto row_val = [&](int R, int c) -> double {
+        if (STAGED) return stage[((R / kChunk) & 1) * kChunk * RL + (R % kChunk) * RL + (w - c)];
+        return *v.row_elem(R, c);
+    };
+    issue(0);
+    issue(1);
+    if (STAGED) cp_async_wait<1>();
     V W[WB + 1][WB + 1];
-    V B[WB][WB + 1];
-    V S[WB][WB];
 #pragma unroll
     for (int r = 0; r <= WB; ++r)
 #pragma unroll
-        for (int c = 0; c <= WB; ++c) W[r][c] = (r <= w && c <= r && r < m) ? A::from(v.a(r, c)) : A::zero();
-#pragma unroll
-    for (int b = 0; b < WB; ++b) {
-#pragma unroll
-        for (int c = 0; c <= WB; ++c) B[b][c] = (b < w && c <= w) ? A::from(v.a(m + b, c)) : A::zero();
-#pragma unroll
-        for (int c = 0; c < WB; ++c) S[b][c] = (b < w && c <= b) ? A::from(v.a(m + b, m + c)) : A::zero();
-    }
-    // rows entering the window one and two columns ahead
-    double nx1[WB + 1], nx2[WB + 1];
-#pragma unroll
-    for (int c = 0; c <= WB; ++c) {
-        const int r1 = 1 + w, r2 = 2 + w;
-        nx1[c] = (c <= w && r1 < m) ? *v.row_elem(r1, c) : 0.0;
-        nx2[c] = (c <= w && r2 < m) ? *v.row_elem(r2, c) : 0.0;
-    }
-    int inf = 0;
+        for (int c = 0; c <= r; ++c) W[r][c] = (r <= w && r < m) ? A::from(v.a(r, c)) : A::zero();
+    int next = 2;  // next chunk to issue
     for (int k = 0; k < m; ++k) {
         const V d = W[0][0];
         if (!A::positive(d)) {
-            inf = k + 1;
-            break;
+            if (STAGED) cp_async_wait<0>();
+            return k + 1;
         }
         const V rs = A::rsqrt_(d);
         v.put_l(k, k, A::to_double(A::mul(d, rs)));
-        V l[WB + 1], lb[WB];
+        V l[WB + 1];
 #pragma unroll
         for (int r = 1; r <= WB; ++r) {
-            l[r] = (r <= w && k + r < m) ? A::mul(W[r][0], rs) : A::zero();
-            if (r <= w && k + r < m) v.put_l(k + r, k, A::to_double(l[r]));
+            const bool on = r <= w && k + r < m;
+            l[r] = on ? A::mul(W[r][0], rs) : A::zero();
+            if (on) v.put_l(k + r, k, A::to_double(l[r]));
         }
-#pragma unroll
-        for (int b = 0; b < WB; ++b) {
-            lb[b] = b < w ? A::mul(B[b][0], rs) : A::zero();
-            if (b < w) v.put_b(b, k, A::to_double(lb[b]));
-        }
-        // rank-1 updates
 #pragma unroll
         for (int r = 1; r <= WB; ++r)
 #pragma unroll
             for (int c = 1; c <= r; ++c) W[r][c] = A::fnma(l[r], l[c], W[r][c]);
 #pragma unroll
-        for (int b = 0; b < WB; ++b) {
-#pragma unroll
-            for (int c = 1; c <= WB; ++c) B[b][c] = A::fnma(lb[b], l[c], B[b][c]);
-#pragma unroll
-            for (int c = 0; c <= b; ++c) S[b][c] = A::fnma(lb[b], lb[c], S[b][c]);
-        }
-        // shift: column k+1 becomes column 0; row k+1+w enters the band
-        // window, column k+1+w enters the border windows
-        const int nc = k + 1 + w;
-#pragma unroll
         for (int r = 0; r < WB; ++r)
 #pragma unroll
             for (int c = 0; c <= r; ++c) W[r][c] = W[r + 1][c + 1];
-#pragma unroll
-        for (int c = 0; c <= WB; ++c) W[WB][c] = A::zero();
-#pragma unroll
-        for (int c = 0; c <= WB; ++c)
-            if (c <= w) {
-#pragma unroll
-                for (int r = 0; r <= WB; ++r)
-                    if (r == w) W[r][c] = A::from(nx1[c]);
+        // row R = k + 1 + w enters the window
+        const int R = k + 1 + w;
+        if (STAGED && R < m && R % kChunk == 0) {
+            // chunk R / kChunk was issued a chunk ago; the buffer of the
+            // chunk before it is free for the one after
+            if (R / kChunk + 1 >= next) {
+                issue(next);
+                ++next;
             }
-#pragma unroll
-        for (int b = 0; b < WB; ++b) {
-#pragma unroll
-            for (int c = 0; c < WB; ++c) B[b][c] = B[b][c + 1];
-            B[b][WB] = A::zero();
-            if (b < w) {
-                const V x = nc < m ? A::from(v.a(m + b, nc)) : A::zero();
-#pragma unroll
-                for (int c = 0; c <= WB; ++c)
-                    if (c == w) B[b][c] = x;
-            }
+            cp_async_wait<1>();
         }
-        // prefetch the row entering two columns from now
-        const int r3 = k + 3 + w;
 #pragma unroll
         for (int c = 0; c <= WB; ++c) {
-            nx1[c] = nx2[c];
-            nx2[c] = (c <= w && r3 < m) ? *v.row_elem(r3, c) : 0.0;
+            const V x = (c <= w && R < m) ? A::from(row_val(R, c)) : A::zero();
+#pragma unroll
+            for (int r = 0; r <= WB; ++r)
+                if (c <= r) {
+                    if (r == w) W[r][c] = x;
+                    if (r == WB && r != w) W[r][c] = A::zero();
+                }
         }
     }
-    if (inf == 0) {
-        // the w x w corner: S = L22 L22^T, in registers
+    if (STAGED) cp_async_wait<0>();
+    return 0;
+}
+
+// Blocks of up to three width classes in one launch: CTAs [0, c0) take
+// items0 (w <= 8, 32 lanes), the next c1 items1 (w <= 12) and the rest
+// items2 (w <= 16), 16 lanes each for those.  Dynamic shared memory holds
+// each lane's staging area (pband storage).
+template <class A, bool DENSE, bool WIDE>
+__global__ void __launch_bounds__(32) k_factor_band_pass(int n0, int n1, int n2, const int32_t *__restrict__ items0,
+                                                         const int32_t *__restrict__ items1,
+                                                         const int32_t *__restrict__ items2,
+                                                         const BlockDesc *__restrict__ blocks, double *__restrict__ out,
+                                                         int32_t *__restrict__ info) {
+    extern __shared__ double dsm[];
+    const int c0 = (n0 + 31) / 32, c1 = (n1 + 15) / 16;
+    int cta = blockIdx.x, list = 0, per = 32;
+    if (cta >= c0) {
+        cta -= c0;
+        list = 1;
+        per = 16;
+        if (cta >= c1) {
+            cta -= c1;
+            list = 2;
+        }
+    }
+    if ((int)threadIdx.x >= per) return;
+    const int idx = cta * per + threadIdx.x;
+    const int nl = list == 0 ? n0 : list == 1 ? n1 : n2;
+    if (idx >= nl) return;
+    const int bi = (list == 0 ? items0 : list == 1 ? items1 : items2)[idx];
+    const BlockDesc bd = blocks[bi];
+    typedef typename ViewOf<DENSE>::T View;
+    const View v = ViewOf<DENSE>::make(out, bd);
+    // lane area: 2 chunks of kChunk rows of up to 9 (list 0) or 17 values,
+    // padded by one double to spread the lanes over the banks
+    const int area = (list == 0 ? 2 * kChunk * 9 : 2 * kChunk * 17) + 1;
+    double *stage = DENSE ? nullptr : dsm + threadIdx.x * area;
+    int res;
+    if constexpr (WIDE) {
+        res = list == 0   ? band_pass<A, 8, View, !DENSE>(v, stage)
+              : list == 1 ? band_pass<A, 12, View, !DENSE>(v, stage)
+                          : band_pass<A, 16, View, !DENSE>(v, stage);
+    } else {
+        res = band_pass<A, 8, View, !DENSE>(v, stage);
+    }
+    info[bi] = res;
+}
+
+template <class A, int G2, int WB, class View, bool STAGED>
+__device__ __forceinline__ void border_pass(const View &v, int t, int gbase, unsigned gmask, double *stage,
+                                            int32_t *info_bi) {
+    typedef typename A::V V;
+    const int w = v.w, m = v.m, RL = w + 1;
+    const int b = t;  // border row m + b
+    const bool used = b < w;
+    // the group's lanes stage the block's L band rows a chunk ahead
+    auto issue = [&](int j) {
+        if (STAGED) {
+            const int r0 = j * kChunk;
+            if (r0 < m) {
+                const int cnt = min(kChunk, m - r0) * RL;
+                double *dst = stage + (j & 1) * kChunk * RL;
+                const double *src = v.row_elem(r0, w);
+                for (int i = t; i < cnt; i += G2) cp_async8(dst + i, src + i);
+            }
+            cp_async_commit();
+        }
+    };
+    auto lval = [&](int k, int col) -> double {  // L[k][col], col in [k-w, k]
+        if (STAGED) return stage[((k / kChunk) & 1) * kChunk * RL + (k % kChunk) * RL + (k - col)];
+        return v.get_l(k, col);
+    };
+    issue(0);
+    issue(1);
+    int next = 2;
+    V y[WB];     // L[m+b][k-w+c], c = 0..w-1
+    V sacc[WB];  // sum_k L[m+b][k] L[m+b'][k], b' <= b
 #pragma unroll
-        for (int j = 0; j < WB; ++j) {
-            if (j < w && inf == 0) {
-                const V dj = S[j][j];
-                if (!A::positive(dj)) {
-                    inf = m + j + 1;
+    for (int c = 0; c < WB; ++c) {
+        y[c] = A::zero();
+        sacc[c] = A::zero();
+    }
+    for (int k = 0; k < m; ++k) {
+        if (STAGED && k % kChunk == 0) {
+            if (k / kChunk + 1 >= next) {
+                issue(next);
+                ++next;
+            }
+            cp_async_wait<1>();
+            __syncwarp(gmask);
+        }
+        // band row k of L11: entries c = 0..w at columns k-w+c (c = w: diagonal)
+        const V e0 = (t <= w && k - w + t >= 0) ? A::from(lval(k, k - w + t)) : A::zero();
+        const int t2 = t + G2;
+        const V e1 = (t2 <= w && k - w + t2 >= 0) ? A::from(lval(k, k - w + t2)) : A::zero();
+        V acc = A::zero();
+        if (used && (k <= b || k >= m + b - w)) acc = A::from(v.a(m + b, k));
+        V diag = A::zero();
+#pragma unroll
+        for (int c = 0; c <= WB; ++c) {
+            if (c > w) break;
+            const V lc = c < G2 ? A::shfl(e0, gbase + c, gmask) : A::shfl(e1, gbase + c - G2, gmask);
+            if (c < w) {
+#pragma unroll
+                for (int cc = 0; cc < WB; ++cc)
+                    if (cc == c) acc = A::fnma(y[cc], lc, acc);
+            } else {
+                diag = lc;
+            }
+        }
+        const V rd = A::rsqrt_(diag);
+        const V val = used ? A::mul(acc, A::mul(rd, rd)) : A::zero();
+        if (used) v.put_b(b, k, A::to_double(val));
+#pragma unroll
+        for (int c = 0; c < WB; ++c) {
+            if (c >= w) break;
+            const V vc = A::shfl(val, gbase + c, gmask);
+            if (c <= b) sacc[c] = A::fma_(val, vc, sacc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c + 1 < WB; ++c) y[c] = y[c + 1];
+#pragma unroll
+        for (int c = 0; c < WB; ++c)
+            if (c == w - 1) y[c] = val;
+        if (STAGED && (k + 1) % kChunk == 0) __syncwarp(gmask);  // chunk consumed by every lane
+    }
+    if (STAGED) cp_async_wait<0>();
+    if (used) {
+#pragma unroll
+        for (int c = 0; c < WB; ++c)
+            if (c <= b) v.put_b(b, m + c, v.a(m + b, m + c) - A::to_double(sacc[c]));
+    }
+    __syncwarp(gmask);
+    if (t == 0) {
+        // dense Cholesky of the w x w corner, FP64
+        int inf = 0;
+        for (int i = 0; i < w && inf == 0; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double s = v.get_b(i, m + j);
+                for (int k = 0; k < j; ++k) s -= v.get_b(i, m + k) * v.get_b(j, m + k);
+                if (j < i) {
+                    v.put_b(i, m + j, s / v.get_b(j, m + j));
                 } else {
-                    const V rs = A::rsqrt_(dj);
-                    S[j][j] = A::mul(dj, rs);
-#pragma unroll
-                    for (int i = j + 1; i < WB; ++i) S[i][j] = A::mul(S[i][j], rs);
-#pragma unroll
-                    for (int i = j + 1; i < WB; ++i)
-#pragma unroll
-                        for (int c = j + 1; c <= i; ++c) S[i][c] = A::fnma(S[i][j], S[c][j], S[i][c]);
+                    if (!(s > 0.0)) {
+                        inf = m + i + 1;
+                        break;
+                    }
+                    v.put_b(i, m + i, sqrt(s));
                 }
             }
         }
-        if (inf == 0) {
-#pragma unroll
-            for (int b = 0; b < WB; ++b)
-#pragma unroll
-                for (int c = 0; c <= b; ++c)
-                    if (b < w) v.put_b(b, m + c, A::to_double(S[b][c]));
-        }
+        *info_bi = inf;
     }
-    info[bi] = inf;
+}
+
+// Pass 2: CTAs [0, c0) run 8-lane groups on items0; the rest 16-lane groups
+// on items1 then items2.  Each group stages its block's L band rows in
+// shared memory (2 chunks).
+template <class A, bool DENSE, bool WIDE>
+__global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int n2, const int32_t *__restrict__ items0,
+                                                            const int32_t *__restrict__ items1,
+                                                            const int32_t *__restrict__ items2,
+                                                            const BlockDesc *__restrict__ blocks,
+                                                            double *__restrict__ out, int32_t *__restrict__ info) {
+    // 16 groups x 2 chunks x kChunk rows x 9 values (8-lane groups, w <= 8),
+    // or 8 groups x 2 x kChunk x 17 (16-lane groups)
+    __shared__ double stg[16 * 2 * kChunk * 9];
+    typedef typename ViewOf<DENSE>::T View;
+    const int c0 = (n0 + 15) / 16;
+    const int lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < c0) {
+        const int t = lane & 7, gbase = lane - t;
+        const unsigned gmask = 0xFFu << gbase;
+        const int grp = threadIdx.x / 8;
+        const int idx = blockIdx.x * 16 + grp;
+        if (idx >= n0) return;
+        const int bi = items0[idx];
+        if (info[bi] != 0) return;  // the band pass found a bad pivot
+        const BlockDesc bd = blocks[bi];
+        const View v = ViewOf<DENSE>::make(out, bd);
+        if (bd.w > 0) border_pass<A, 8, 8, View, !DENSE>(v, t, gbase, gmask, stg + grp * 2 * kChunk * 9, info + bi);
+        return;
+    }
+    if constexpr (WIDE) {
+        const int t = lane & 15, gbase = lane - t;
+        const unsigned gmask = 0xFFFFu << gbase;
+        const int grp = threadIdx.x / 16;
+        const int idx = (blockIdx.x - c0) * 8 + grp;
+        if (idx >= n1 + n2) return;
+        const int bi = idx < n1 ? items1[idx] : items2[idx - n1];
+        if (info[bi] != 0) return;
+        const BlockDesc bd = blocks[bi];
+        const View v = ViewOf<DENSE>::make(out, bd);
+        border_pass<A, 16, 16, View, !DENSE>(v, t, gbase, gmask, stg + grp * 2 * kChunk * 17, info + bi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 factorisation on a shadow of the band.
+//
+// The band rows are converted once to an FP32 copy (coalesced), the band
+// pass eliminates on that copy, the L11 rows are converted back once, and
+// the border pass reads the FP32 rows; no conversion sits inside the
+// elimination loops.  Kernels are specialised on the exact band width W
+// (a CTA only holds blocks of one width), so every window index is static.
+// ---------------------------------------------------------------------------
+
+// One CTA-sized slice of a width class: blocks items[first .. first+count).
+struct F32Cta {
+    int32_t w, first, count, pad;
+};
+
+__global__ void k_f32_shadow_in(const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
+                                const double *__restrict__ out, float *__restrict__ sh) {
+    const BlockDesc bd = blocks[items[blockIdx.x]];
+    const int64_t cnt = (int64_t)bd.n * (bd.w + 1);
+    const double *src = out + bd.off_pband;
+    float *dst = sh + bd.off_pband;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = f64_to_f32_bits(src[i]);
+}
+
+// L11 rows (row < m, band offset d <= row) back to the FP64 blocks buffer.
+__global__ void k_f32_shadow_out(const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
+                                 const int32_t *__restrict__ info, const float *__restrict__ sh,
+                                 double *__restrict__ out) {
+    const int bi = items[blockIdx.x];
+    if (info[bi] != 0) return;
+    const BlockDesc bd = blocks[bi];
+    const int RL = bd.w + 1, m = bd.n - bd.w;
+    const int64_t cnt = (int64_t)m * RL;
+    const float *src = sh + bd.off_pband;
+    double *dst = out + bd.off_pband;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int row = (int)(i / RL), d = (int)(i % RL);
+        if (d <= row) dst[i] = f32_to_f64_bits(src[i]);
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Band pass on the FP32 shadow, one lane per block, exact width W.
+// band: the block's shadow rows (row i at band + i (W+1), entry d = column
+// i - d); stage: this lane's 2 x kChunk x (W+1) floats.
+template <int W>
+__device__ __forceinline__ int f32_band(float *band, int m, float *stage) {
+    constexpr int RL = W + 1;
+    auto issue = [&](int j) {
+        const int r0 = j * kChunk;
+        if (r0 < m) {
+            const int cnt = min(kChunk, m - r0) * RL;
+            float *dst = stage + (j & 1) * kChunk * RL;
+            const float *src = band + (int64_t)r0 * RL;
+            for (int i = 0; i < cnt; ++i) cp_async4(dst + i, src + i);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    float Wn[W + 1][W + 1];
+#pragma unroll
+    for (int r = 0; r <= W; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[(int64_t)r * RL + (r - c)] : 0.0f;
+    cp_async_wait<1>();
+    int next = 2;
+    for (int k = 0; k < m; ++k) {
+        const float d = Wn[0][0];
+        if (!(d > 0.0f)) {
+            cp_async_wait<0>();
+            return k + 1;
+        }
+        const float rs = rsqrtf(d);
+        band[(int64_t)k * RL] = d * rs;
+        float l[W + 1];
+#pragma unroll
+        for (int r = 1; r <= W; ++r) {
+            l[r] = k + r < m ? Wn[r][0] * rs : 0.0f;
+            if (k + r < m) band[(int64_t)(k + r) * RL + r] = l[r];
+        }
+#pragma unroll
+        for (int r = 1; r <= W; ++r)
+#pragma unroll
+            for (int c = 1; c <= r; ++c) Wn[r][c] = fmaf(-l[r], l[c], Wn[r][c]);
+#pragma unroll
+        for (int r = 0; r < W; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c) Wn[r][c] = Wn[r + 1][c + 1];
+        const int R = k + 1 + W;  // row entering the window
+        if (R < m && R % kChunk == 0) {
+            if (R / kChunk + 1 >= next) {
+                issue(next);
+                ++next;
+            }
+            cp_async_wait<1>();
+        }
+        const float *row = stage + ((R / kChunk) & 1) * kChunk * RL + (R % kChunk) * RL;
+#pragma unroll
+        for (int c = 0; c <= W; ++c) Wn[W][c] = R < m ? row[W - c] : 0.0f;
+    }
+    cp_async_wait<0>();
+    return 0;
+}
+
+template <int W>
+struct F32BandDispatch {
+    __device__ static int run(int w, float *band, int m, float *stage) {
+        if (w == W) return f32_band<W>(band, m, stage);
+        return F32BandDispatch<W - 1>::run(w, band, m, stage);
+    }
+};
+template <>
+struct F32BandDispatch<0> {
+    __device__ static int run(int w, float *band, int m, float *stage) {
+        return w == 0 ? f32_band<0>(band, m, stage) : -1;
+    }
+};
+
+// One CTA per F32Cta slice: 32 lanes for W <= 8, 16 lanes above.
+__global__ void __launch_bounds__(32) k_f32_band_pass(const F32Cta *__restrict__ ctas,
+                                                      const int32_t *__restrict__ items,
+                                                      const BlockDesc *__restrict__ blocks, float *__restrict__ sh,
+                                                      int32_t *__restrict__ info) {
+    extern __shared__ float fsm[];
+    const F32Cta c = ctas[blockIdx.x];
+    if ((int)threadIdx.x >= c.count) return;
+    const int bi = items[c.first + threadIdx.x];
+    const BlockDesc bd = blocks[bi];
+    float *stage = fsm + threadIdx.x * (2 * kChunk * (c.w + 1) + 1);
+    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, stage);
+}
+
+// Border pass, G2 lanes (one per border row) per block, exact width W.
+// The group stages the block's FP32 L11 rows; every lane reads the whole
+// band row k from shared memory (broadcast), forms its L[m+b][k], and
+// accumulates the corner row S[b][.]; one lane factors the W x W corner.
+template <int W, int G2>
+__device__ __forceinline__ void f32_border(const BlockDesc &bd, const float *__restrict__ sband, double *__restrict__ out,
+                                           int t, unsigned gmask, float *stage, int32_t *info_bi) {
+    constexpr int RL = W + 1;
+    const int n = bd.n, m = n - W;
+    const PBandView v{out + bd.off_pband, out + bd.off_pband + (int64_t)n * RL, n, W, m};
+    const int b = t;
+    const bool used = b < W;
+    auto issue = [&](int j) {
+        const int r0 = j * kChunk;
+        if (r0 < m) {
+            const int cnt = min(kChunk, m - r0) * RL;
+            float *dst = stage + (j & 1) * kChunk * RL;
+            const float *src = sband + (int64_t)r0 * RL;
+            for (int i = t; i < cnt; i += G2) cp_async4(dst + i, src + i);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    int next = 2;
+    float y[W];
+    float sacc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+        y[c] = 0.0f;
+        sacc[c] = 0.0f;
+    }
+    for (int k = 0; k < m; ++k) {
+        if (k % kChunk == 0) {
+            if (k / kChunk + 1 >= next) {
+                issue(next);
+                ++next;
+            }
+            cp_async_wait<1>();
+            __syncwarp(gmask);
+            // write this chunk's L11 rows (entries d <= row) to the FP64 blocks
+            const int rows = min(kChunk, m - k);
+            const float *cs = stage + ((k / kChunk) & 1) * kChunk * RL;
+            double *dst = out + bd.off_pband + (int64_t)k * RL;
+            for (int i = t; i < rows * RL; i += G2) {
+                const int rr = i / RL, d = i - rr * RL;
+                if (d <= k + rr) dst[i] = f32_to_f64_bits(cs[i]);
+            }
+        }
+        const float *row = stage + ((k / kChunk) & 1) * kChunk * RL + (k % kChunk) * RL;
+        // L[k][k-W+c] = row[W-c]; entries left of column 0 are zero
+        float acc = 0.0f;
+        if (used && (k <= b || k >= m + b - W)) acc = f64_to_f32_bits(v.a(m + b, k));
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const float lc = k - W + c >= 0 ? row[W - c] : 0.0f;
+            acc = fmaf(-y[c], lc, acc);
+        }
+        const float rd = rsqrtf(row[0]);
+        const float val = used ? acc * (rd * rd) : 0.0f;
+        if (used) v.put_b(b, k, f32_to_f64_bits(val));
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const float vc = __shfl_sync(gmask, val, (threadIdx.x & 31) - t + c);
+            if (c <= b) sacc[c] = fmaf(val, vc, sacc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c + 1 < W; ++c) y[c] = y[c + 1];
+        y[W - 1] = val;
+        if ((k + 1) % kChunk == 0) __syncwarp(gmask);
+    }
+    cp_async_wait<0>();
+    if (used) {
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+            if (c <= b) v.put_b(b, m + c, v.a(m + b, m + c) - f32_to_f64_bits(sacc[c]));
+    }
+    __syncwarp(gmask);
+    if (t == 0) {
+        int inf = 0;
+        for (int i = 0; i < W && inf == 0; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double s = v.get_b(i, m + j);
+                for (int k = 0; k < j; ++k) s -= v.get_b(i, m + k) * v.get_b(j, m + k);
+                if (j < i) {
+                    v.put_b(i, m + j, s / v.get_b(j, m + j));
+                } else {
+                    if (!(s > 0.0)) {
+                        inf = m + i + 1;
+                        break;
+                    }
+                    v.put_b(i, m + i, sqrt(s));
+                }
+            }
+        }
+        *info_bi = inf;
+    }
+}
+
+template <int W>
+struct F32BorderDispatch {
+    __device__ static void run(int w, const BlockDesc &bd, const float *sband, double *out, int t, unsigned gmask,
+                               float *stage, int32_t *info_bi) {
+        if (w == W) {
+            if constexpr (W <= 8)
+                f32_border<W, 8>(bd, sband, out, t, gmask, stage, info_bi);
+            else
+                f32_border<W, 16>(bd, sband, out, t, gmask, stage, info_bi);
+            return;
+        }
+        F32BorderDispatch<W - 1>::run(w, bd, sband, out, t, gmask, stage, info_bi);
+    }
+};
+template <>
+struct F32BorderDispatch<0> {
+    __device__ static void run(int w, const BlockDesc &bd, const float *sband, double *out, int t, unsigned,
+                               float *, int32_t *) {
+        if (w != 0) return;
+        for (int i = t; i < bd.n; i += 8) out[bd.off_pband + i] = f32_to_f64_bits(sband[i]);  // diagonal block
+    }
+};
+
+// One CTA per F32Cta slice: 16 groups of 8 lanes (W <= 8) or 8 groups of 16.
+__global__ void __launch_bounds__(128) k_f32_border_pass(const F32Cta *__restrict__ ctas,
+                                                         const int32_t *__restrict__ items,
+                                                         const BlockDesc *__restrict__ blocks,
+                                                         const float *__restrict__ sh, double *__restrict__ out,
+                                                         int32_t *__restrict__ info) {
+    __shared__ float stg[16 * 2 * kChunk * 9];  // = 8 x 2 x kChunk x 17 + 32 floats
+    const F32Cta c = ctas[blockIdx.x];
+    const int G2 = c.w <= 8 ? 8 : 16;
+    const int lane = threadIdx.x & 31;
+    const int t = lane % G2, grp = threadIdx.x / G2;
+    const unsigned gmask = (G2 == 8 ? 0xFFu : 0xFFFFu) << (lane - t);
+    if (grp >= c.count) return;
+    const int bi = items[c.first + grp];
+    if (info[bi] != 0) return;
+    const BlockDesc bd = blocks[bi];
+    F32BorderDispatch<16>::run(bd.w, bd, sh + bd.off_pband, out, t, gmask, stg + grp * 2 * kChunk * (c.w + 1),
+                               info + bi);
 }
 
 // One warp per dense-format block: right-looking, FP64, in place.
@@ -508,35 +935,45 @@ __global__ void k_factor_serial(int nitems, const int32_t *__restrict__ items, c
 
 using namespace sympix;
 
-// FP32 keeps the whole elimination state of a block in one lane's registers;
-// FP64 and split FP32 need twice the registers and use lane groups.
+// FP32 runs both passes for every band width up to 16; FP64 and split FP32
+// (twice the registers) run them for w <= 8 and factor wider bands with
+// lane groups.
 template <class A>
 static void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st) {
-    constexpr bool lane_kernel = std::is_same<A, ArF32>::value;
-    const int n16 = (int)pl->factor_items[0].size(), n32 = (int)pl->factor_items[1].size();
-    if constexpr (lane_kernel) {
-        if (n16) {
-            const unsigned grid = (unsigned)((n16 + 31) / 32);
-            if (dense)
-                k_factor_lane<A, 8, true><<<grid, 32, 0, st>>>(n16, pl->d_factor_items[0].p, pl->d_blocks.p, blocks,
-                                                               info);
-            else
-                k_factor_lane<A, 8, false><<<grid, 32, 0, st>>>(n16, pl->d_factor_items[0].p, pl->d_blocks.p, blocks,
-                                                                info);
+    constexpr bool wide = std::is_same<A, ArF32>::value;
+    const int n0 = (int)pl->factor_items[0].size();
+    const int n1 = (int)pl->factor_items[1].size(), n2 = (int)pl->factor_items[2].size();
+    const int w1 = wide ? n1 : 0, w2 = wide ? n2 : 0;
+    const int32_t *i0 = pl->d_factor_items[0].p, *i1 = pl->d_factor_items[1].p, *i2 = pl->d_factor_items[2].p;
+    if (n0 + w1 + w2 > 0) {
+        const unsigned g1 = (unsigned)((n0 + 31) / 32 + (w1 + 15) / 16 + (w2 + 15) / 16);
+        const unsigned g2 = (unsigned)((n0 + 15) / 16 + (w1 + w2 + 7) / 8);
+        const size_t smem = (size_t)32 * (2 * kChunk * 17 + 1) * sizeof(double);
+        if (dense) {
+            k_factor_band_pass<A, true, wide><<<g1, 32, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info);
+            k_factor_border_pass<A, true, wide><<<g2, 128, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info);
+        } else {
+            cudaFuncSetAttribute(k_factor_band_pass<A, false, wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            k_factor_band_pass<A, false, wide><<<g1, 32, smem, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks,
+                                                                     info);
+            k_factor_border_pass<A, false, wide><<<g2, 128, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks,
+                                                                     info);
         }
-    } else if (n16) {
-        const unsigned grid = (unsigned)((n16 * 16 + 127) / 128);
-        if (dense)
-            k_factor_band<A, 16, true><<<grid, 128, 0, st>>>(n16, pl->d_factor_items[0].p, pl->d_blocks.p, blocks, info);
-        else
-            k_factor_band<A, 16, false><<<grid, 128, 0, st>>>(n16, pl->d_factor_items[0].p, pl->d_blocks.p, blocks, info);
     }
-    if (n32) {
-        const unsigned grid = (unsigned)((n32 * 32 + 127) / 128);
-        if (dense)
-            k_factor_band<A, 32, true><<<grid, 128, 0, st>>>(n32, pl->d_factor_items[1].p, pl->d_blocks.p, blocks, info);
-        else
-            k_factor_band<A, 32, false><<<grid, 128, 0, st>>>(n32, pl->d_factor_items[1].p, pl->d_blocks.p, blocks, info);
+    if constexpr (!wide) {
+        // wider bands: lane groups of 32 (band and border in one pass)
+        for (int l = 1; l <= 2; ++l) {
+            const int nl = (int)pl->factor_items[l].size();
+            if (!nl) continue;
+            const unsigned grid = (unsigned)((nl * 32 + 127) / 128);
+            if (dense)
+                k_factor_band<A, 32, true><<<grid, 128, 0, st>>>(nl, pl->d_factor_items[l].p, pl->d_blocks.p, blocks,
+                                                                info);
+            else
+                k_factor_band<A, 32, false><<<grid, 128, 0, st>>>(nl, pl->d_factor_items[l].p, pl->d_blocks.p, blocks,
+                                                                 info);
+        }
     }
 }
 
@@ -551,16 +988,28 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
     const bool dense = storage == SYMPIX_STORE_DENSE;
     if (precision == SYMPIX_PREC_FP64)
         launch_band<ArF64>(pl, dense, blocks, info, st);
-    else if (precision == SYMPIX_PREC_FP32)
+    else if (precision == SYMPIX_PREC_FP32 && !dense) {
+        const int nf = (int)pl->f32_items.size();
+        if (nf) {
+            k_f32_shadow_in<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow.p);
+            const size_t smem = (size_t)32 * (2 * kChunk * 9 + 1) * sizeof(float);
+            k_f32_band_pass<<<(unsigned)pl->f32_band_ctas.size(), 32, smem, st>>>(
+                (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info);
+            if (!pl->f32_border_ctas.empty())
+                k_f32_border_pass<<<(unsigned)pl->f32_border_ctas.size(), 128, 0, st>>>(
+                    (const F32Cta *)pl->d_f32_border_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p,
+                    blocks, info);
+        }
+    } else if (precision == SYMPIX_PREC_FP32)
         launch_band<ArF32>(pl, dense, blocks, info, st);
     else
         launch_band<ArF2>(pl, dense, blocks, info, st);
-    const int nd = (int)pl->factor_items[2].size(), ns = (int)pl->factor_items[3].size();
+    const int nd = (int)pl->factor_items[3].size(), ns = (int)pl->factor_items[4].size();
     if (nd)
-        k_factor_dense<<<(unsigned)((nd * 32 + 127) / 128), 128, 0, st>>>(nd, pl->d_factor_items[2].p, pl->d_blocks.p,
+        k_factor_dense<<<(unsigned)((nd * 32 + 127) / 128), 128, 0, st>>>(nd, pl->d_factor_items[3].p, pl->d_blocks.p,
                                                                         blocks, dense ? 1 : 0, info);
     if (ns)
-        k_factor_serial<<<(unsigned)((ns + 31) / 32), 32, 0, st>>>(ns, pl->d_factor_items[3].p, pl->d_blocks.p, blocks,
+        k_factor_serial<<<(unsigned)((ns + 31) / 32), 32, 0, st>>>(ns, pl->d_factor_items[4].p, pl->d_blocks.p, blocks,
                                                                   dense ? 1 : 0, info);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_factor_blocks: launch");

@@ -128,9 +128,14 @@ struct sympix_plan_s {
     // sampling schedule (built once)
     std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
     std::vector<SampleItem> items_dense;
-    // factorisation work lists, each most expensive first: [0] band w <= 8,
-    // [1] band 8 < w <= 16, [2] dense format n <= 1024, [3] everything else
-    std::vector<int32_t> factor_items[4];
+    // factorisation work lists, each most expensive first: periodic band with
+    // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16; [3] dense format with
+    // n <= 1024; [4] everything else
+    std::vector<int32_t> factor_items[5];
+    // FP32 factorisation on a band shadow: periodic-band blocks with w <= 16
+    // grouped by exact width, and CTA slices of the band and border passes
+    std::vector<int32_t> f32_items;
+    std::vector<int4> f32_band_ctas, f32_border_ctas;  // (w, first, count, 0)
     // device
     sympix::DevBuf<CanonPair> d_pairs;
     sympix::DevBuf<double> d_slot_u;         // u = 1 - cos(gamma) per slot
@@ -145,6 +150,9 @@ struct sympix_plan_s {
     sympix::DevBuf<PairEntry> d_entries;
     sympix::DevBuf<SampleItem> d_items_pband[5];
     sympix::DevBuf<SampleItem> d_items_dense;
-    sympix::DevBuf<int32_t> d_factor_items[4];
+    sympix::DevBuf<int32_t> d_factor_items[5];
+    sympix::DevBuf<int32_t> d_f32_items;
+    sympix::DevBuf<int4> d_f32_band_ctas, d_f32_border_ctas;
+    sympix::DevBuf<float> d_shadow;  // FP32 copy of the band rows
     bool table_ready = false;
 };

@@ -334,18 +334,38 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         const BlockDesc &bd = pl->blocks[b];
         int list;
         if (bd.format == SYMPIX_BLOCK_PBAND)
-            list = bd.w <= 8 ? 0 : bd.w <= 16 ? 1 : 3;
+            list = bd.w <= 8 ? 0 : bd.w <= 12 ? 1 : bd.w <= 16 ? 2 : 4;
         else
-            list = bd.n <= 1024 ? 2 : 3;
+            list = bd.n <= 1024 ? 3 : 4;
         pl->factor_items[list].push_back(b);
     }
 
+    // FP32 factorisation on a band shadow: blocks by exact width, CTA slices
+    {
+        std::vector<int32_t> byw[17];
+        for (int b : order) {
+            const BlockDesc &bd = pl->blocks[b];
+            if (bd.format == SYMPIX_BLOCK_PBAND && bd.w <= 16) byw[bd.w].push_back(b);
+        }
+        for (int w = 0; w <= 16; ++w) {
+            const int first = (int)pl->f32_items.size(), cnt = (int)byw[w].size();
+            pl->f32_items.insert(pl->f32_items.end(), byw[w].begin(), byw[w].end());
+            const int pb = w <= 8 ? 32 : 16, pr = w <= 8 ? 16 : 8;
+            for (int i = 0; i < cnt; i += pb) pl->f32_band_ctas.push_back(make_int4(w, first + i, std::min(pb, cnt - i), 0));
+            for (int i = 0; i < cnt; i += pr)
+                pl->f32_border_ctas.push_back(make_int4(w, first + i, std::min(pr, cnt - i), 0));
+        }
+    }
+    if ((rc = pl->d_f32_items.upload(pl->f32_items)) || (rc = pl->d_f32_band_ctas.upload(pl->f32_band_ctas)) ||
+        (rc = pl->d_f32_border_ctas.upload(pl->f32_border_ctas)) ||
+        (rc = pl->d_shadow.alloc(std::max<int64_t>(pl->size_pband, 1))))
+        return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
         (rc = pl->d_items_dense.upload(pl->items_dense)))
         return fail(rc);
     for (int bkt = 0; bkt < 5; ++bkt)
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
-    for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < 5; ++l)
         if ((rc = pl->d_factor_items[l].upload(pl->factor_items[l]))) return fail(rc);
     const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
     const size_t nn = (size_t)nops * grid->npix;
@@ -379,8 +399,9 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int32_t *tabl
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
     if (sample) *sample = s;
-    int f = 0;
-    for (int l = 0; l < 4; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    // band and border passes (one launch each), dense-format and fallback
+    int f = (pl->factor_items[0].empty() && pl->factor_items[1].empty() && pl->factor_items[2].empty()) ? 0 : 2;
+    for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
     if (factor) *factor = f;
     return SYMPIX_OK;
 }
