@@ -127,6 +127,14 @@ void sympix_grid_free(sympix_grid_t grid);
 int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, int ring1,
                    sympix_plan_t *out);
 
+/* Plan options (sympix_plan_option). */
+#define SYMPIX_OPT_FP32_PIVOT_FLOOR 1 /* FP32 factor: a block is refactored in FP64 when a pivot
+                                          falls below floor x its row's original diagonal
+                                          (default 0.05; 0 never, > 1 always) */
+
+/* Set a plan option; takes effect for the following calls on the plan. */
+int sympix_plan_option(sympix_plan_t plan, int option, double value);
+
 /* Counts of a plan (any pointer may be NULL): nslots symmetry-class slots
  * (kernel values per operator); npairs coupled ordered ring pairs summed over
  * operators; ntriples the pixel triples (q, r, p) with r in the stored lower
@@ -136,10 +144,11 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
 int sympix_plan_counts(sympix_plan_t plan, int64_t *nslots, int64_t *npairs, int64_t *ntriples,
                        int64_t *nmults);
 
-/* Number of kernel launches one call of sympix_kernel_table,
- * sympix_sample_blocks (for `storage`) and sympix_factor_blocks enqueues. */
-int sympix_plan_launches(sympix_plan_t plan, int storage, int32_t *table, int32_t *sample,
-                         int32_t *factor);
+/* Number of library kernel launches one call of sympix_kernel_table,
+ * sympix_sample_blocks and sympix_factor_blocks enqueues for a storage mode
+ * and the contraction / factor arithmetic (SYMPIX_PREC_*). */
+int sympix_plan_launches(sympix_plan_t plan, int storage, int sample_precision, int factor_precision,
+                         int32_t *table, int32_t *sample, int32_t *factor);
 
 /* Output size of sample/factor for a storage mode: bytes of the blocks
  * buffer (doubles) and the number of stored lower-triangle elements
@@ -226,8 +235,12 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
 /* Cholesky-factor every sampled block in place, M = L L^T.
  *   precision  arithmetic of the periodic-band factorisation:
  *              SYMPIX_PREC_FP64, SYMPIX_PREC_FP32X2 (split FP32, near-FP64
- *              accuracy on the FP32 pipes) or SYMPIX_PREC_FP32.  Dense-format
- *              blocks and bands wider than 16 are factored in FP64 always.
+ *              accuracy on the FP32 pipes) or SYMPIX_PREC_FP32.  With FP32
+ *              (PBAND storage) a block whose pivots shrink below the plan's
+ *              pivot floor (SYMPIX_OPT_FP32_PIVOT_FLOOR) relative to their
+ *              original diagonal is near-degenerate and is refactored in FP64
+ *              on the device.  Dense-format blocks and bands wider than 16
+ *              are factored in FP64 always.
  *   info       device int32 [nops * nblocks] (operator-major, blocks in ring
  *              order): 0, or i+1 for the first row i whose pivot is not
  *              positive (that block's factor is then incomplete).

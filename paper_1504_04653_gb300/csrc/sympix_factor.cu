@@ -80,6 +80,12 @@ struct ViewOf<true> {
     }
 };
 
+// info value of a block whose FP32 pivots shrank below the floor: it is
+// refactored in FP64 from the untouched FP64 input (kRescued marks a
+// rescued block between the FP64 band and border passes).
+constexpr int32_t kRescue = 0x40000000;
+constexpr int32_t kRescued = 0x20000000;
+
 // Asynchronous global -> shared copies (no register round trip), used to
 // prefetch band rows several elimination steps ahead.
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
@@ -99,7 +105,7 @@ constexpr int kRing = 8;      // ring slots per group (> kPrefetch)
 template <class A, int G, bool DENSE>
 __global__ void __launch_bounds__(128) k_factor_band(int nitems, const int32_t *__restrict__ items,
                                                      const BlockDesc *__restrict__ blocks, double *__restrict__ out,
-                                                     int32_t *__restrict__ info) {
+                                                     int32_t *__restrict__ info, int rescue) {
     typedef typename A::V V;
     constexpr int HW = G / 2;
     constexpr int RB = (G == 16) ? 8 : 2;  // corner rows per pass
@@ -110,6 +116,7 @@ __global__ void __launch_bounds__(128) k_factor_band(int nitems, const int32_t *
     const int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
     if (idx >= nitems) return;  // uniform within the group
     const int bi = items[idx];
+    if (rescue && info[bi] != kRescue) return;  // uniform within the group
     const BlockDesc bd = blocks[bi];
     const typename ViewOf<DENSE>::T v = ViewOf<DENSE>::make(out, bd);
     const int w = bd.w, m = bd.n - bd.w;
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(32) k_factor_band_pass(int n0, int n1, int n2,
                                                          const int32_t *__restrict__ items1,
                                                          const int32_t *__restrict__ items2,
                                                          const BlockDesc *__restrict__ blocks, double *__restrict__ out,
-                                                         int32_t *__restrict__ info) {
+                                                         int32_t *__restrict__ info, int rescue) {
     extern __shared__ double dsm[];
     const int c0 = (n0 + 31) / 32, c1 = (n1 + 15) / 16;
     int cta = blockIdx.x, list = 0, per = 32;
@@ -392,6 +399,7 @@ __global__ void __launch_bounds__(32) k_factor_band_pass(int n0, int n1, int n2,
     const int nl = list == 0 ? n0 : list == 1 ? n1 : n2;
     if (idx >= nl) return;
     const int bi = (list == 0 ? items0 : list == 1 ? items1 : items2)[idx];
+    if (rescue && info[bi] != kRescue) return;
     const BlockDesc bd = blocks[bi];
     typedef typename ViewOf<DENSE>::T View;
     const View v = ViewOf<DENSE>::make(out, bd);
@@ -407,7 +415,7 @@ __global__ void __launch_bounds__(32) k_factor_band_pass(int n0, int n1, int n2,
     } else {
         res = band_pass<A, 8, View, !DENSE>(v, stage);
     }
-    info[bi] = res;
+    info[bi] = (rescue && res == 0) ? kRescued : res;
 }
 
 template <class A, int G2, int WB, class View, bool STAGED>
@@ -525,7 +533,9 @@ __global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int 
                                                             const int32_t *__restrict__ items1,
                                                             const int32_t *__restrict__ items2,
                                                             const BlockDesc *__restrict__ blocks,
-                                                            double *__restrict__ out, int32_t *__restrict__ info) {
+                                                            double *__restrict__ out, int32_t *__restrict__ info,
+                                                            int rescue) {
+    const int32_t want = rescue ? kRescued : 0;
     // 16 groups x 2 chunks x kChunk rows x 9 values (8-lane groups, w <= 8),
     // or 8 groups x 2 x kChunk x 17 (16-lane groups)
     __shared__ double stg[16 * 2 * kChunk * 9];
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int 
         const int idx = blockIdx.x * 16 + grp;
         if (idx >= n0) return;
         const int bi = items0[idx];
-        if (info[bi] != 0) return;  // the band pass found a bad pivot
+        if (info[bi] != want) return;  // a bad pivot in the band pass, or not this pass's block
         const BlockDesc bd = blocks[bi];
         const View v = ViewOf<DENSE>::make(out, bd);
         if (bd.w > 0) border_pass<A, 8, 8, View, !DENSE>(v, t, gbase, gmask, stg + grp * 2 * kChunk * 9, info + bi);
@@ -552,7 +562,7 @@ __global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int 
         const int idx = (blockIdx.x - c0) * 8 + grp;
         if (idx >= n1 + n2) return;
         const int bi = idx < n1 ? items1[idx] : items2[idx - n1];
-        if (info[bi] != 0) return;
+        if (info[bi] != want) return;
         const BlockDesc bd = blocks[bi];
         const View v = ViewOf<DENSE>::make(out, bd);
         border_pass<A, 16, 16, View, !DENSE>(v, t, gbase, gmask, stg + grp * 2 * kChunk * 17, info + bi);
@@ -609,7 +619,7 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 // band: the block's shadow rows (row i at band + i (W+1), entry d = column
 // i - d); stage: this lane's 2 x kChunk x (W+1) floats.
 template <int W>
-__device__ __forceinline__ int f32_band(float *band, int m, float *stage) {
+__device__ __forceinline__ int f32_band(float *band, int m, float *stage, float floor) {
     constexpr int RL = W + 1;
     auto issue = [&](int j) {
         const int r0 = j * kChunk;
@@ -624,17 +634,20 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage) {
     issue(0);
     issue(1);
     float Wn[W + 1][W + 1];
+    float od[W + 1];  // original diagonal of the window rows
 #pragma unroll
-    for (int r = 0; r <= W; ++r)
+    for (int r = 0; r <= W; ++r) {
 #pragma unroll
         for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[(int64_t)r * RL + (r - c)] : 0.0f;
+        od[r] = Wn[r][r];
+    }
     cp_async_wait<1>();
     int next = 2;
     for (int k = 0; k < m; ++k) {
         const float d = Wn[0][0];
-        if (!(d > 0.0f)) {
+        if (!(d > floor * od[0])) {  // includes d <= 0: FP64 decides
             cp_async_wait<0>();
-            return k + 1;
+            return kRescue;
         }
         const float rs = rsqrtf(d);
         band[(int64_t)k * RL] = d * rs;
@@ -663,6 +676,9 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage) {
         const float *row = stage + ((R / kChunk) & 1) * kChunk * RL + (R % kChunk) * RL;
 #pragma unroll
         for (int c = 0; c <= W; ++c) Wn[W][c] = R < m ? row[W - c] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < W; ++r) od[r] = od[r + 1];
+        od[W] = Wn[W][W];
     }
     cp_async_wait<0>();
     return 0;
@@ -670,15 +686,15 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage) {
 
 template <int W>
 struct F32BandDispatch {
-    __device__ static int run(int w, float *band, int m, float *stage) {
-        if (w == W) return f32_band<W>(band, m, stage);
-        return F32BandDispatch<W - 1>::run(w, band, m, stage);
+    __device__ static int run(int w, float *band, int m, float *stage, float floor) {
+        if (w == W) return f32_band<W>(band, m, stage, floor);
+        return F32BandDispatch<W - 1>::run(w, band, m, stage, floor);
     }
 };
 template <>
 struct F32BandDispatch<0> {
-    __device__ static int run(int w, float *band, int m, float *stage) {
-        return w == 0 ? f32_band<0>(band, m, stage) : -1;
+    __device__ static int run(int w, float *band, int m, float *stage, float floor) {
+        return w == 0 ? f32_band<0>(band, m, stage, floor) : -1;
     }
 };
 
@@ -686,14 +702,14 @@ struct F32BandDispatch<0> {
 __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Cta *__restrict__ ctas,
                                                       const int32_t *__restrict__ items,
                                                       const BlockDesc *__restrict__ blocks, float *__restrict__ sh,
-                                                      int32_t *__restrict__ info) {
+                                                      int32_t *__restrict__ info, float floor) {
     extern __shared__ float fsm[];
     const F32Cta c = ctas[blockIdx.x];
     if ((int)threadIdx.x >= c.count) return;
     const int bi = items[c.first + threadIdx.x];
     const BlockDesc bd = blocks[bi];
     float *stage = fsm + threadIdx.x * (2 * kChunk * (c.w + 1) + 1);
-    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, stage);
+    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, stage, floor);
 }
 
 // Border pass, G2 lanes (one per border row) per block, exact width W.
@@ -939,7 +955,8 @@ using namespace sympix;
 // (twice the registers) run them for w <= 8 and factor wider bands with
 // lane groups.
 template <class A>
-static void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st) {
+static void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st,
+                        int rescue = 0) {
     constexpr bool wide = std::is_same<A, ArF32>::value;
     const int n0 = (int)pl->factor_items[0].size();
     const int n1 = (int)pl->factor_items[1].size(), n2 = (int)pl->factor_items[2].size();
@@ -950,15 +967,17 @@ static void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *i
         const unsigned g2 = (unsigned)((n0 + 15) / 16 + (w1 + w2 + 7) / 8);
         const size_t smem = (size_t)32 * (2 * kChunk * 17 + 1) * sizeof(double);
         if (dense) {
-            k_factor_band_pass<A, true, wide><<<g1, 32, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info);
-            k_factor_border_pass<A, true, wide><<<g2, 128, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info);
+            k_factor_band_pass<A, true, wide><<<g1, 32, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info,
+                                                                 rescue);
+            k_factor_border_pass<A, true, wide><<<g2, 128, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks, info,
+                                                                    rescue);
         } else {
             cudaFuncSetAttribute(k_factor_band_pass<A, false, wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
             k_factor_band_pass<A, false, wide><<<g1, 32, smem, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks,
-                                                                     info);
+                                                                     info, rescue);
             k_factor_border_pass<A, false, wide><<<g2, 128, 0, st>>>(n0, w1, w2, i0, i1, i2, pl->d_blocks.p, blocks,
-                                                                     info);
+                                                                     info, rescue);
         }
     }
     if constexpr (!wide) {
@@ -969,10 +988,10 @@ static void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *i
             const unsigned grid = (unsigned)((nl * 32 + 127) / 128);
             if (dense)
                 k_factor_band<A, 32, true><<<grid, 128, 0, st>>>(nl, pl->d_factor_items[l].p, pl->d_blocks.p, blocks,
-                                                                info);
+                                                                info, rescue);
             else
                 k_factor_band<A, 32, false><<<grid, 128, 0, st>>>(nl, pl->d_factor_items[l].p, pl->d_blocks.p, blocks,
-                                                                 info);
+                                                                 info, rescue);
         }
     }
 }
@@ -994,11 +1013,14 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
             k_f32_shadow_in<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow.p);
             const size_t smem = (size_t)32 * (2 * kChunk * 9 + 1) * sizeof(float);
             k_f32_band_pass<<<(unsigned)pl->f32_band_ctas.size(), 32, smem, st>>>(
-                (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info);
+                (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info,
+                (float)pl->fp32_pivot_floor);
             if (!pl->f32_border_ctas.empty())
                 k_f32_border_pass<<<(unsigned)pl->f32_border_ctas.size(), 128, 0, st>>>(
                     (const F32Cta *)pl->d_f32_border_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p,
                     blocks, info);
+            // near-degenerate blocks: FP64 from the untouched FP64 input
+            launch_band<ArF64>(pl, false, blocks, info, st, 1);
         }
     } else if (precision == SYMPIX_PREC_FP32)
         launch_band<ArF32>(pl, dense, blocks, info, st);

@@ -155,4 +155,5 @@ struct sympix_plan_s {
     sympix::DevBuf<int4> d_f32_band_ctas, d_f32_border_ctas;
     sympix::DevBuf<float> d_shadow;  // FP32 copy of the band rows
     bool table_ready = false;
+    double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
 };

@@ -380,6 +380,17 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     return SYMPIX_OK;
 }
 
+extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_option: NULL plan");
+    if (option == SYMPIX_OPT_FP32_PIVOT_FLOOR) {
+        if (!(value >= 0.0) || !std::isfinite(value))
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: pivot floor must be finite and >= 0");
+        pl->fp32_pivot_floor = value;
+        return SYMPIX_OK;
+    }
+    return set_error(SYMPIX_EINVAL, "sympix_plan_option: unknown option %d", option);
+}
+
 extern "C" int sympix_plan_counts(sympix_plan_t pl, int64_t *nslots, int64_t *npairs, int64_t *ntriples,
                                   int64_t *nmults) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_counts: NULL plan");
@@ -390,17 +401,37 @@ extern "C" int sympix_plan_counts(sympix_plan_t pl, int64_t *nslots, int64_t *np
     return SYMPIX_OK;
 }
 
-extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int32_t *table, int32_t *sample,
-                                    int32_t *factor) {
+extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_precision, int factor_precision,
+                                    int32_t *table, int32_t *sample, int32_t *factor) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_launches: NULL plan");
-    if (table) *table = pl->nslots > 0 ? 1 + (pl->nops + 3) / 4 : 1;
-    int s = storage == SYMPIX_STORE_DENSE ? 1 : 0;  // the zero fill
-    s += 1;                                          // the N^-1 split (FP32 arithmetics)
+    if (table) {
+        int chunks = 0;
+        for (int op0 = 0; op0 < pl->nops;) {
+            const int left = pl->nops - op0;
+            op0 += left >= 4 ? 4 : left >= 2 ? 2 : 1;
+            ++chunks;
+        }
+        *table = 1 + (pl->nslots > 0 ? chunks : 0);
+    }
+    int s = sample_precision != SYMPIX_PREC_FP64 ? 1 : 0;  // the N^-1 split
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
     if (sample) *sample = s;
-    // band and border passes (one launch each), dense-format and fallback
-    int f = (pl->factor_items[0].empty() && pl->factor_items[1].empty() && pl->factor_items[2].empty()) ? 0 : 2;
+    int f = 0;
+    const bool band = !(pl->factor_items[0].empty() && pl->factor_items[1].empty() && pl->factor_items[2].empty());
+    if (factor_precision == SYMPIX_PREC_FP32 && storage == SYMPIX_STORE_PBAND) {
+        // shadow copy, band and border passes, and the FP64 rescue launches
+        // (which return at once for blocks that need no rescue)
+        f = pl->f32_items.empty() ? 0 : 3;
+        if (band) {
+            f += 2;
+            for (int l = 1; l <= 2; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+        }
+    } else if (band) {
+        f = 2;
+        if (factor_precision != SYMPIX_PREC_FP32)
+            for (int l = 1; l <= 2; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    }
     for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
     if (factor) *factor = f;
     return SYMPIX_OK;

@@ -17,6 +17,7 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+OPT_FP32_PIVOT_FLOOR = 1
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
@@ -52,8 +53,9 @@ SIGNATURES = [
     ("sympix_grid_copy", _i, [_vp, _dp, _i32p, _i64p, _i32p]),
     ("sympix_grid_free", None, [_vp]),
     ("sympix_support", _i, [_vp, _i, _dp, _i, _i, ctypes.POINTER(_vp)]),
+    ("sympix_plan_option", _i, [_vp, _i, ctypes.c_double]),
     ("sympix_plan_counts", _i, [_vp, _i64p, _i64p, _i64p, _i64p]),
-    ("sympix_plan_launches", _i, [_vp, _i, _i32p, _i32p, _i32p]),
+    ("sympix_plan_launches", _i, [_vp, _i, _i, _i, _i32p, _i32p, _i32p]),
     ("sympix_blocks_size", _i, [_vp, _i, _sizep, _i64p]),
     ("sympix_block_layout", _i, [_vp, _i, _i, _i, _i64p, _i32p, _i32p, _i32p]),
     ("sympix_support_copy", _i, [_vp, _i, _i, _i, _i32p]),
@@ -180,10 +182,15 @@ class Plan:
                                          ctypes.byref(n), ctypes.byref(w), ctypes.byref(fmt)))
         return off.value, n.value, w.value, fmt.value
 
-    def launches(self, storage="pband"):
+    def set_pivot_floor(self, value: float):
+        """FP32 factor: blocks whose pivots shrink below value x diagonal go to FP64."""
+        _check(lib().sympix_plan_option(self._h, OPT_FP32_PIVOT_FLOOR, float(value)))
+
+    def launches(self, storage="pband", sample_precision="fp32", factor_precision="fp32"):
         """Kernel launches of (kernel_table, sample_blocks, factor_blocks)."""
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(lib().sympix_plan_launches(self._h, STORAGES[storage], ctypes.byref(a), ctypes.byref(b),
+        _check(lib().sympix_plan_launches(self._h, STORAGES[storage], PRECISIONS[sample_precision],
+                                          PRECISIONS[factor_precision], ctypes.byref(a), ctypes.byref(b),
                                           ctypes.byref(c)))
         return a.value, b.value, c.value
 

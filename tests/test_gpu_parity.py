@@ -332,3 +332,27 @@ def test_factor_precisions_lmax500(S, dev, fprec, storage):
         if ref.shape[0] <= 400:
             Lref, _ = O.cholesky(ref)
             assert _err(L, Lref) <= 1000 * tol, (j, _err(L, Lref))
+
+
+@pytest.mark.parametrize("floor", [0.0, 2.0])
+def test_fp32_factor_fp64_rescue(S, dev, floor):
+    """floor 2 sends every block through the FP64 rescue (FP64 accuracy),
+    floor 0 none (FP32 accuracy)."""
+    import torch
+    wl = W.WORKLOADS["lmax500"]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    plan.set_pivot_floor(floor)
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    ninv_h = wl.ninv(colat)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(ninv_h, device=dev), precision="fp64")
+    info = S.sympix_factor_blocks(plan, blocks, precision="fp32")
+    fac = blocks.cpu().numpy()
+    assert np.all(info.cpu().numpy() == 0)
+    og = O.grid(wl.lmax)
+    tol = 1e-12 if floor > 1 else 1e-6
+    for j in (0, 5, 250, 499):
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv_h[0], j)
+        L = S.unpack_block(fac, plan, "pband", 0, j, factored=True)
+        assert _err(L @ L.T, ref) <= 10 * tol, (j, _err(L @ L.T, ref))
