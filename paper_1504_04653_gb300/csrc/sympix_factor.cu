@@ -3,26 +3,30 @@
 // A periodic-band block (half-width w, 2w+1 < n) couples only |i-j| <= w or
 // |i-j| >= n-w.  With m = n - w its leading m x m part A11 is a plain band
 // matrix, so L11 keeps the band; the last w rows (the border) fill in
-// completely.  Right-looking elimination of column k touches only rows
-// k+1..k+w of the band and the w border rows, so one lane group carries
-// the whole active part in registers:
-//   * window lanes r = 0..w-1 hold rows k+1+r of A11 at columns k..k+1+r;
-//   * border lanes r = 0..w-1 hold border row m+r at columns k..k+w;
-//   * the pivot is row k's updated diagonal, broadcast to the group.
-// Each step forms 1/sqrt(pivot), scales column k (L[k+1+r][k] and
-// L[m+r][k]), applies the rank-1 update to the band columns k+1..k+w and
-// shifts the window by one row, loading one new row of the band.  The
-// border lanes thus do the forward substitution L21 = A21 L11^-T in the
-// same instructions.  Afterwards the group forms the corner
-// S = A22 - L21 L21^T with lanes over the column index and factors it.
-// Work O(n w^2) per block instead of O(n^3).
+// completely.  Work is O(n w^2) per block instead of O(n^3):
+//   L11 L11^T = A11,   L21 = A21 L11^-T,   L22 L22^T = A22 - L21 L21^T.
 //
-// Arithmetic: FP64, split FP32 (near-FP64 on the FP32 pipes) or FP32.
-// Dense-format blocks (small or fully coupled rings) use a warp-parallel
-// right-looking dense factorisation in FP64; blocks wider than the lane
-// groups allow fall back to one thread per block.
+// Kernels, by band width and arithmetic (the plan sorts blocks into lists):
+//   w <= 8 (FP64, split FP32) and w <= 16 (FP32 on pband storage):
+//       two passes.  The band pass runs one lane per block with the active
+//       (w+1) x (w+1) triangle in registers and band rows staged into
+//       shared memory a chunk ahead with cp.async; the border pass runs one
+//       lane per border row (the forward substitution) and accumulates the
+//       corner S on the fly, then one lane factors the w x w corner.
+//       FP32 eliminates on a float copy of the band (the "shadow"),
+//       converted once on the way in and once on the way out.
+//   8 < w <= 16 (FP64, split FP32): one group of 32 lanes per block carries
+//       the band window and the border rows in registers, one column per
+//       step (band and border in one pass).
+//   16 < w <= 64: one CTA per block, window, border columns and S in shared
+//       memory indexed mod (w+1).
+//   dense storage with n <= 1024: a warp per block, right-looking, FP64;
+//   anything else: one thread per block, FP64.
 //
-// A non-positive pivot stops the block and records info = row + 1.
+// FP32 rescue: an FP32 elimination whose pivot falls below a floor times the
+// original diagonal marks its block, and the block is refactored in FP64
+// from the untouched FP64 input.  A non-positive pivot in FP64 stops the
+// block and records info = row + 1.
 #include <type_traits>
 
 #include "sympix_arith.cuh"
@@ -452,8 +456,25 @@ __device__ __forceinline__ void border_pass(const View &v, int t, int gbase, uns
         y[c] = A::zero();
         sacc[c] = A::zero();
     }
+    const int kband = ((m - w) / kChunk) * kChunk;
     for (int k = 0; k < m; ++k) {
         if (STAGED && k % kChunk == 0) {
+            // exact zeros in every lane's window: skip to the band part
+            if (k > w && k < kband) {
+                bool zero = true;
+#pragma unroll
+                for (int c = 0; c < WB; ++c) zero = zero && A::to_double(y[c]) == 0.0;
+                if (__all_sync(gmask, zero)) {
+                    if (used)
+                        for (int kk = k; kk < kband; ++kk) v.put_b(b, kk, 0.0);
+                    k = kband;
+                    cp_async_wait<0>();
+                    __syncwarp(gmask);
+                    issue(k / kChunk);
+                    issue(k / kChunk + 1);
+                    next = k / kChunk + 2;
+                }
+            }
             if (k / kChunk + 1 >= next) {
                 issue(next);
                 ++next;
@@ -593,10 +614,14 @@ __global__ void k_f32_shadow_in(const int32_t *__restrict__ items, const BlockDe
     for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = f64_to_f32_bits(src[i]);
 }
 
-// L11 rows (row < m, band offset d <= row) back to the FP64 blocks buffer.
-__global__ void k_f32_shadow_out(const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
-                                 const int32_t *__restrict__ info, const float *__restrict__ sh,
-                                 double *__restrict__ out) {
+// L11 rows (row < m, entries d <= row) back to the FP64 blocks.  The band is
+// one contiguous run of m (w+1) values: thread t copies elements t, t + T,
+// t + 2T, ..., tracking (row, offset) by constant strides, so consecutive
+// threads touch consecutive addresses.
+__global__ void __launch_bounds__(256) k_f32_shadow_out(const int32_t *__restrict__ items,
+                                                        const BlockDesc *__restrict__ blocks,
+                                                        const int32_t *__restrict__ info,
+                                                        const float *__restrict__ sh, double *__restrict__ out) {
     const int bi = items[blockIdx.x];
     if (info[bi] != 0) return;
     const BlockDesc bd = blocks[bi];
@@ -604,9 +629,17 @@ __global__ void k_f32_shadow_out(const int32_t *__restrict__ items, const BlockD
     const int64_t cnt = (int64_t)m * RL;
     const float *src = sh + bd.off_pband;
     double *dst = out + bd.off_pband;
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int row = (int)(i / RL), d = (int)(i % RL);
-        if (d <= row) dst[i] = f32_to_f64_bits(src[i]);
+    const int T = blockDim.x;
+    const int drow = T / RL, dd = T % RL;
+    int row = threadIdx.x / RL, d = threadIdx.x % RL;
+    for (int64_t e = threadIdx.x; e < cnt; e += T) {
+        if (d <= row) dst[e] = f32_to_f64_bits(src[e]);
+        row += drow;
+        d += dd;
+        if (d >= RL) {
+            d -= RL;
+            ++row;
+        }
     }
 }
 
@@ -744,22 +777,35 @@ __device__ __forceinline__ void f32_border(const BlockDesc &bd, const float *__r
         y[c] = 0.0f;
         sacc[c] = 0.0f;
     }
+    // A21 is nonzero only in the first W columns (wrap) and the last W
+    // (band); in between the substitution only propagates what the wrap
+    // part started, which decays geometrically.  Once every lane's window
+    // holds exact FP32 zeros each further column is exactly zero, so the
+    // group jumps to the band part and writes the zeros directly.
+    const int kband = ((m - W) / kChunk) * kChunk;  // chunk-aligned, <= first band-part column
     for (int k = 0; k < m; ++k) {
         if (k % kChunk == 0) {
+            if (k > W && k < kband) {
+                bool zero = true;
+#pragma unroll
+                for (int c = 0; c < W; ++c) zero = zero && (y[c] == 0.0f);
+                if (__all_sync(gmask, zero)) {
+                    if (used)
+                        for (int kk = k; kk < kband; ++kk) v.put_b(b, kk, 0.0);
+                    k = kband;
+                    cp_async_wait<0>();
+                    __syncwarp(gmask);
+                    issue(k / kChunk);
+                    issue(k / kChunk + 1);
+                    next = k / kChunk + 2;
+                }
+            }
             if (k / kChunk + 1 >= next) {
                 issue(next);
                 ++next;
             }
             cp_async_wait<1>();
             __syncwarp(gmask);
-            // write this chunk's L11 rows (entries d <= row) to the FP64 blocks
-            const int rows = min(kChunk, m - k);
-            const float *cs = stage + ((k / kChunk) & 1) * kChunk * RL;
-            double *dst = out + bd.off_pband + (int64_t)k * RL;
-            for (int i = t; i < rows * RL; i += G2) {
-                const int rr = i / RL, d = i - rr * RL;
-                if (d <= k + rr) dst[i] = f32_to_f64_bits(cs[i]);
-            }
         }
         const float *row = stage + ((k / kChunk) & 1) * kChunk * RL + (k % kChunk) * RL;
         // L[k][k-W+c] = row[W-c]; entries left of column 0 are zero
@@ -827,11 +873,8 @@ struct F32BorderDispatch {
 };
 template <>
 struct F32BorderDispatch<0> {
-    __device__ static void run(int w, const BlockDesc &bd, const float *sband, double *out, int t, unsigned,
-                               float *, int32_t *) {
-        if (w != 0) return;
-        for (int i = t; i < bd.n; i += 8) out[bd.off_pband + i] = f32_to_f64_bits(sband[i]);  // diagonal block
-    }
+    __device__ static void run(int, const BlockDesc &, const float *, double *, int, unsigned, float *,
+                               int32_t *) {}
 };
 
 // One CTA per F32Cta slice: 16 groups of 8 lanes (W <= 8) or 8 groups of 16.
@@ -852,6 +895,218 @@ __global__ void __launch_bounds__(128) k_f32_border_pass(const F32Cta *__restric
     const BlockDesc bd = blocks[bi];
     F32BorderDispatch<16>::run(bd.w, bd, sh + bd.off_pband, out, t, gmask, stg + grp * 2 * kChunk * (c.w + 1),
                                info + bi);
+}
+
+// ---------------------------------------------------------------------------
+// Wide bands (16 < w <= 64): one CTA per block.
+//
+// The active band window (rows k..k+w, columns k..k+w), the w border rows at
+// columns k..k+w and the corner accumulator S live in shared memory; rows
+// and columns are stored at index mod (w+1), so moving the window to column
+// k+1 costs nothing: the slot of row/column k is reused for k+1+w.  Per
+// column: thread 0 forms the pivot, the threads scale the column (band and
+// border), then apply the rank-1 update to the band window, the border rows
+// and S while the next band row and border column, loaded one column ahead,
+// go into the freed slots.  T = double or float; the float version sends a
+// block whose pivot falls below the floor to the FP64 rescue.
+// ---------------------------------------------------------------------------
+constexpr int kWideMax = 64;
+
+template <typename T>
+__device__ __forceinline__ T wide_from(double x);
+template <>
+__device__ __forceinline__ double wide_from<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float wide_from<float>(double x) { return f64_to_f32_bits(x); }
+__device__ __forceinline__ double wide_to(double x) { return x; }
+__device__ __forceinline__ double wide_to(float x) { return f32_to_f64_bits(x); }
+
+// Where the wide kernel writes L: straight into the FP64 blocks (FP64), or
+// into the FP32 band shadow, copied to the FP64 blocks only once the block
+// has factored without reaching the pivot floor (so an FP64 rescue still
+// finds its input intact).
+template <typename T, class View>
+struct WideSink;
+template <class View>
+struct WideSink<double, View> {
+    View v;
+    __device__ void put_l(int i, int j, double x) const { v.put_l(i, j, x); }
+    __device__ void put_b(int b, int j, double x) const { v.put_b(b, j, x); }
+    __device__ double get_b(int b, int j) const { return v.get_b(b, j); }
+};
+template <class View>
+struct WideSink<float, View> {
+    float *band;  // shadow: n x (w+1) band, then w x n border
+    int n, w;
+    __device__ void put_l(int i, int j, float x) const { band[(int64_t)i * (w + 1) + (i - j)] = x; }
+    __device__ void put_b(int b, int j, float x) const { band[(int64_t)n * (w + 1) + (int64_t)b * n + j] = x; }
+    __device__ double get_b(int b, int j) const {
+        return f32_to_f64_bits(band[(int64_t)n * (w + 1) + (int64_t)b * n + j]);
+    }
+};
+
+template <typename T, bool DENSE>
+__global__ void __launch_bounds__(256) k_factor_wide(int nitems, const int32_t *__restrict__ items,
+                                                     const BlockDesc *__restrict__ blocks, double *__restrict__ out,
+                                                     int32_t *__restrict__ info, int rescue, float floor,
+                                                     float *__restrict__ shadow) {
+    extern __shared__ double wsm_raw[];
+    T *wsm = reinterpret_cast<T *>(wsm_raw);
+    const int bi = items[blockIdx.x];
+    if (rescue && info[bi] != kRescue) return;
+    const BlockDesc bd = blocks[bi];
+    typedef typename ViewOf<DENSE>::T View;
+    const View v = ViewOf<DENSE>::make(out, bd);
+    const int w = bd.w, m = bd.n - bd.w, S = w + 1;
+    auto make_sink = [&]() {
+        if constexpr (sizeof(T) == 4)
+            return WideSink<T, View>{shadow + bd.off_pband, bd.n, w};
+        else
+            return WideSink<T, View>{v};
+    };
+    const WideSink<T, View> sink = make_sink();
+    T *Wn = wsm;         // S x S, [row mod S][col mod S]
+    T *Bd = Wn + S * S;  // w x S, [b][col mod S]
+    T *Sc = Bd + w * S;  // w x w corner accumulator
+    T *lc = Sc + w * w;  // S: column k of L (band rows k..k+w)
+    T *lb = lc + S;      // w: column k of L (border rows)
+    T *od = lb + w;      // S: original diagonal of the window rows
+    __shared__ T piv;
+    __shared__ int fail;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < S * S; e += nt) {
+        const int r = e / S, c = e % S;
+        Wn[e] = (c <= r && r < m) ? wide_from<T>(v.a(r, c)) : T(0);
+        if (c == r) od[r] = Wn[e];
+    }
+    for (int e = tid; e < w * S; e += nt) {
+        const int b = e / S, c = e % S;
+        Bd[e] = c < m ? wide_from<T>(v.a(m + b, c)) : T(0);
+    }
+    for (int e = tid; e < w * w; e += nt) {
+        const int b = e / w, c = e % w;
+        Sc[e] = c <= b ? wide_from<T>(v.a(m + b, m + c)) : T(0);
+    }
+    if (tid == 0) fail = 0;
+    const int nband = w * (w + 1) / 2, nbord = w * w, ncorner = w * (w + 1) / 2;
+    const int e0 = nband + nbord + ncorner, total = e0 + S;
+    // the new-row element this thread stores each column (c < S), if any
+    int myc = -1;
+    for (int e = tid; e < total; e += nt)
+        if (e >= e0) myc = e - e0;
+    auto fetch = [&](int nc, T &pa, T &pb) {
+        pa = (myc >= 0 && nc < m) ? wide_from<T>(v.a(nc, nc - w + myc)) : T(0);
+        pb = (myc >= 0 && myc < w && nc < m) ? wide_from<T>(v.a(m + myc, nc)) : T(0);
+    };
+    T pa, pb;
+    fetch(1 + w, pa, pb);
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        const int ks = k % S;
+        if (tid == 0) {
+            const T d = Wn[ks * S + ks];
+            if (!(d > T(floor) * od[ks])) {
+                fail = (sizeof(T) == 4) ? kRescue : k + 1;
+            } else {
+                const T lkk = sqrt(d);
+                piv = T(1) / lkk;
+                sink.put_l(k, k, lkk);
+            }
+        }
+        __syncthreads();
+        if (fail) break;
+        const T rs = piv;
+        for (int r = tid; r < S + w; r += nt) {
+            if (r == 0) {
+                lc[0] = T(0);
+            } else if (r <= w) {
+                const int row = k + r;
+                const T l = row < m ? Wn[(row % S) * S + ks] * rs : T(0);
+                lc[r] = l;
+                if (row < m) sink.put_l(row, k, l);
+            } else {
+                const int b = r - S;
+                const T l = Bd[b * S + ks] * rs;
+                lb[b] = l;
+                sink.put_b(b, k, l);
+            }
+        }
+        __syncthreads();
+        const int nc = k + 1 + w;
+        for (int e = tid; e < total; e += nt) {
+            if (e < nband) {
+                int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f) + 1;
+                while (r * (r - 1) / 2 > e) --r;
+                while ((r + 1) * r / 2 <= e) ++r;
+                const int c = e - r * (r - 1) / 2 + 1;
+                const int row = k + r;
+                if (row < m) Wn[(row % S) * S + (k + c) % S] -= lc[r] * lc[c];
+            } else if (e < nband + nbord) {
+                const int f = e - nband, b = f / w, c = f % w + 1;
+                Bd[b * S + (k + c) % S] -= lb[b] * lc[c];
+            } else if (e < e0) {
+                const int f = e - nband - nbord;
+                int b = (int)((sqrtf(8.0f * f + 1.0f) - 1.0f) * 0.5f);
+                while (b * (b + 1) / 2 > f) --b;
+                while ((b + 1) * (b + 2) / 2 <= f) ++b;
+                const int c = f - b * (b + 1) / 2;
+                Sc[b * w + c] -= lb[b] * lb[c];
+            } else {
+                // band row nc (columns k+1..nc) and the border rows' column nc
+                // into the slot freed by row/column k
+                const int c = e - e0;
+                if (nc < m) {
+                    Wn[ks * S + (k + 1 + c) % S] = pa;
+                    if (c == w) od[ks] = pa;
+                }
+                if (c < w) Bd[c * S + ks] = pb;
+            }
+        }
+        fetch(nc + 1, pa, pb);
+        __syncthreads();
+    }
+    if (fail) {
+        if (tid == 0) info[bi] = fail;
+        return;
+    }
+    __shared__ int cinf;
+    if (tid == 0) {
+        // the w x w corner, FP64 arithmetic
+        int inf = 0;
+        for (int i = 0; i < w && inf == 0; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double s = wide_to(Sc[i * w + j]);
+                for (int q = 0; q < j; ++q) s -= sink.get_b(i, m + q) * sink.get_b(j, m + q);
+                if (j < i) {
+                    sink.put_b(i, m + j, T(s / sink.get_b(j, m + j)));
+                } else {
+                    if (!(s > 0.0)) {
+                        inf = m + i + 1;
+                        break;
+                    }
+                    sink.put_b(i, m + i, T(sqrt(s)));
+                }
+            }
+        }
+        if (sizeof(T) == 4 && inf) inf = kRescue;  // let FP64 decide
+        cinf = inf;
+        info[bi] = inf;
+    }
+    if constexpr (sizeof(T) == 4) {
+        // the block factored in FP32: copy L from the shadow
+        __syncthreads();
+        if (cinf) return;
+        const int64_t nb = (int64_t)m * S;  // band rows < m
+        for (int64_t e = tid; e < nb; e += nt) {
+            const int row = (int)(e / S), d = (int)(e % S);
+            if (d <= row) out[bd.off_pband + e] = f32_to_f64_bits(sink.band[e]);
+        }
+        const int64_t bo = (int64_t)bd.n * S;
+        for (int64_t e = tid; e < (int64_t)w * bd.n; e += nt) {
+            const int b = (int)(e / bd.n), j = (int)(e % bd.n);
+            if (j <= m + b) out[bd.off_pband + bo + e] = f32_to_f64_bits(sink.band[bo + e]);
+        }
+    }
 }
 
 // One warp per dense-format block: right-looking, FP64, in place.
@@ -1015,6 +1270,7 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
             k_f32_band_pass<<<(unsigned)pl->f32_band_ctas.size(), 32, smem, st>>>(
                 (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info,
                 (float)pl->fp32_pivot_floor);
+            k_f32_shadow_out<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow.p, blocks);
             if (!pl->f32_border_ctas.empty())
                 k_f32_border_pass<<<(unsigned)pl->f32_border_ctas.size(), 128, 0, st>>>(
                     (const F32Cta *)pl->d_f32_border_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p,
@@ -1026,6 +1282,28 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
         launch_band<ArF32>(pl, dense, blocks, info, st);
     else
         launch_band<ArF2>(pl, dense, blocks, info, st);
+    const int nw = (int)pl->factor_items[5].size();
+    if (nw) {
+        const size_t smem = (size_t)((kWideMax + 1) * (kWideMax + 1) + kWideMax * (kWideMax + 1) +
+                                     kWideMax * kWideMax + 3 * (kWideMax + 1)) *
+                            sizeof(double);
+        const int32_t *it = pl->d_factor_items[5].p;
+        // FP32 arithmetic for the FP32 factor (near-degenerate blocks then
+        // rescued in FP64), FP64 otherwise
+        if (precision == SYMPIX_PREC_FP32 && !dense) {
+            auto kf = k_factor_wide<float, false>;
+            auto kd = dense ? k_factor_wide<double, true> : k_factor_wide<double, false>;
+            cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kf<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 0, (float)pl->fp32_pivot_floor,
+                                      pl->d_shadow.p);
+            kd<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 1, 0.0f, nullptr);
+        } else {
+            auto kd = dense ? k_factor_wide<double, true> : k_factor_wide<double, false>;
+            cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kd<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 0, 0.0f, nullptr);
+        }
+    }
     const int nd = (int)pl->factor_items[3].size(), ns = (int)pl->factor_items[4].size();
     if (nd)
         k_factor_dense<<<(unsigned)((nd * 32 + 127) / 128), 128, 0, st>>>(nd, pl->d_factor_items[3].p, pl->d_blocks.p,

@@ -129,9 +129,9 @@ struct sympix_plan_s {
     std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
     std::vector<SampleItem> items_dense;
     // factorisation work lists, each most expensive first: periodic band with
-    // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16; [3] dense format with
-    // n <= 1024; [4] everything else
-    std::vector<int32_t> factor_items[5];
+    // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16, [5] 16 < w <= 64;
+    // [3] dense format with n <= 1024; [4] everything else
+    std::vector<int32_t> factor_items[6];
     // FP32 factorisation on a band shadow: periodic-band blocks with w <= 16
     // grouped by exact width, and CTA slices of the band and border passes
     std::vector<int32_t> f32_items;
@@ -150,7 +150,7 @@ struct sympix_plan_s {
     sympix::DevBuf<PairEntry> d_entries;
     sympix::DevBuf<SampleItem> d_items_pband[5];
     sympix::DevBuf<SampleItem> d_items_dense;
-    sympix::DevBuf<int32_t> d_factor_items[5];
+    sympix::DevBuf<int32_t> d_factor_items[6];
     sympix::DevBuf<int32_t> d_f32_items;
     sympix::DevBuf<int4> d_f32_band_ctas, d_f32_border_ctas;
     sympix::DevBuf<float> d_shadow;  // FP32 copy of the band rows

@@ -334,7 +334,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         const BlockDesc &bd = pl->blocks[b];
         int list;
         if (bd.format == SYMPIX_BLOCK_PBAND)
-            list = bd.w <= 8 ? 0 : bd.w <= 12 ? 1 : bd.w <= 16 ? 2 : 4;
+            list = bd.w <= 8 ? 0 : bd.w <= 12 ? 1 : bd.w <= 16 ? 2 : bd.w <= 64 ? 5 : 4;
         else
             list = bd.n <= 1024 ? 3 : 4;
         pl->factor_items[list].push_back(b);
@@ -365,7 +365,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         return fail(rc);
     for (int bkt = 0; bkt < 5; ++bkt)
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
-    for (int l = 0; l < 5; ++l)
+    for (int l = 0; l < 6; ++l)
         if ((rc = pl->d_factor_items[l].upload(pl->factor_items[l]))) return fail(rc);
     const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
     const size_t nn = (size_t)nops * grid->npix;
@@ -432,7 +432,8 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
         if (factor_precision != SYMPIX_PREC_FP32)
             for (int l = 1; l <= 2; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
     }
-    for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    for (int l = 3; l < 6; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    if (factor_precision == SYMPIX_PREC_FP32 && !pl->factor_items[5].empty()) ++f;  // wide FP64 rescue
     if (factor) *factor = f;
     return SYMPIX_OK;
 }

@@ -356,3 +356,26 @@ def test_fp32_factor_fp64_rescue(S, dev, floor):
         ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv_h[0], j)
         L = S.unpack_block(fac, plan, "pband", 0, j, factored=True)
         assert _err(L @ L.T, ref) <= 10 * tol, (j, _err(L @ L.T, ref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_wide_operators(S, dev, precision):
+    """Several operators in one plan with beams wide enough for band widths
+    above 16 (the wide-band factor and the wide-beam contraction)."""
+    wl = W.Workload("wide", 200, [90.0, 150.0, 240.0, 360.0], [10.0, 0.0, 25.0, 5.0], [11, 12, 13, 14])
+    r = _run(S, dev, wl, precision=precision, factor=True)
+    plan = r["plan"]
+    og = O.grid(wl.lmax)
+    widths = [plan.block_layout("pband", o, 100)[2] for o in range(4)]
+    assert max(widths) > 16, widths
+    tol = TOL[precision]
+    for o in range(4):
+        for j in (0, 3, 47, 100, 200):
+            ref, _ = O.block(og, wl.beams()[o], wl.priors()[o], wl.radii()[o], r["ninv"][o], j)
+            M = S.unpack_block(r["sampled"], plan, "pband", o, j)
+            assert _err(M, ref) <= tol, (o, j, _err(M, ref))
+            _, info = O.cholesky(ref)
+            assert r["info"][o * 201 + j] == info, (o, j)
+            if info == 0:
+                L = S.unpack_block(r["factored"], plan, "pband", o, j, factored=True)
+                assert _err(L @ L.T, ref) <= 10 * tol, (o, j, _err(L @ L.T, ref))
