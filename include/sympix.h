@@ -62,6 +62,13 @@ extern "C" {
 
 typedef struct sympix_grid_s *sympix_grid_t;
 typedef struct sympix_plan_s *sympix_plan_t;
+typedef struct sympix_step_s *sympix_step_t;
+
+/* stages of a captured step (sympix_step_launch) */
+#define SYMPIX_STAGE_TABLE 1  /* sympix_kernel_table  */
+#define SYMPIX_STAGE_SAMPLE 2 /* sympix_sample_blocks */
+#define SYMPIX_STAGE_FACTOR 4 /* sympix_factor_blocks */
+#define SYMPIX_STAGE_ALL 7
 
 typedef struct {
     int lmax;       /* band limit the grid was built for                    */
@@ -239,8 +246,9 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
  *              (PBAND storage) a block whose pivots shrink below the plan's
  *              pivot floor (SYMPIX_OPT_FP32_PIVOT_FLOOR) relative to their
  *              original diagonal is near-degenerate and is refactored in FP64
- *              on the device.  Dense-format blocks and bands wider than 16
- *              are factored in FP64 always.
+ *              on the device.  Dense-format blocks (small or fully coupled
+ *              rings) are factored in FP64 always; with FP32X2, bands wider
+ *              than 16 are factored in FP64.
  *   info       device int32 [nops * nblocks] (operator-major, blocks in ring
  *              order): 0, or i+1 for the first row i whose pivot is not
  *              positive (that block's factor is then incomplete).
@@ -249,6 +257,37 @@ int sympix_factor_blocks(sympix_plan_t plan, int storage, int precision, double 
                          void *stream);
 
 void sympix_plan_free(sympix_plan_t plan);
+
+/* ------------------------------------------------------------------------ */
+/* Captured step (batching: one graph launch per stage)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Capture the three calls above -- sympix_kernel_table(bl, dl),
+ * sympix_sample_blocks(ninv, sample_precision, storage, blocks) and
+ * sympix_factor_blocks(storage, factor_precision, blocks, info) -- into one
+ * CUDA graph per stage on the current device, and instantiate them.  Nothing
+ * runs.  The graphs keep the pointers: a replay reads bl, dl and ninv as they
+ * are when it runs, so callers update inputs in place between replays.  The
+ * device buffers, and the plan, must outlive the step.  The plan's scratch
+ * (FP32 copies of N^-1, the factor's band shadow) is shared by the plan's
+ * steps and direct calls: work on one plan must not overlap on the GPU.
+ * Allocates the table's coefficient staging if no call has yet.  The paper
+ * describes the method, not its launch; this is the grouped, graph-replayed
+ * execution of the same three operations. */
+int sympix_step_create(sympix_plan_t plan, const double *bl, const double *dl, const double *ninv,
+                       int storage, int sample_precision, int factor_precision, double *blocks,
+                       int32_t *info, sympix_step_t *out);
+
+/* Replay the stages in `stages` (SYMPIX_STAGE_* bits, in the order table,
+ * sample, factor) on `stream` (any stream of the step's device, including
+ * the default stream).  Sampling without the table stage requires the plan's
+ * table to have been computed.  Asynchronous. */
+int sympix_step_launch(sympix_step_t step, int stages, void *stream);
+
+/* Number of kernel launches one replay of `stages` performs. */
+int sympix_step_kernels(sympix_step_t step, int stages, int64_t *count);
+
+void sympix_step_free(sympix_step_t step);
 
 /* Text of the calling thread's last error ("" if none). */
 const char *sympix_last_error(void);

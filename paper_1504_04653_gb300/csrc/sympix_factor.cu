@@ -28,6 +28,7 @@
 // from the untouched FP64 input.  A non-positive pivot in FP64 stops the
 // block and records info = row + 1.
 #include <type_traits>
+#include <utility>
 
 #include "sympix_arith.cuh"
 #include "sympix_internal.cuh"
@@ -648,73 +649,108 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
+// f(integral_constant<int, I>) for I = B .. E-1, expanded at compile time.
+template <int B, int E>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &f) {
+        f(std::integral_constant<int, B>{});
+        StaticFor<B + 1, E>::run(f);
+    }
+};
+template <int E>
+struct StaticFor<E, E> {
+    template <class F>
+    __device__ __forceinline__ static void run(F &) {}
+};
+
 // Band pass on the FP32 shadow, one lane per block, exact width W.
+//
+// The active window is the lower triangle of rows k..k+W at columns k..k+r
+// (row k+r).  Row i and column j are kept in register slot i mod (W+1) and
+// j mod (W+1), and the column loop is unrolled by one period of W+1 steps,
+// so every slot index is static and moving the window costs nothing: the
+// row retiring at step k frees the slot the row k+1+W enters.  During
+// period p (steps k = p(W+1) .. p(W+1)+W) the entering rows are exactly the
+// W+1 rows of period p+1, staged into shared memory with cp.async one
+// period ahead.  Inside a period the code is straight-line, so the
+// scheduler overlaps the next pivot's rsqrt with the rest of the update.
+// Pivots are checked against the floor once per period: a block that fell
+// below it is recomputed from its FP64 input anyway.
+//
 // band: the block's shadow rows (row i at band + i (W+1), entry d = column
-// i - d); stage: this lane's 2 x kChunk x (W+1) floats.
+// i - d); stage: this lane's two period buffers, lane-interleaved (element
+// e at stage[32 e]) so that the lanes' loads hit distinct banks.
 template <int W>
 __device__ __forceinline__ int f32_band(float *band, int m, float *stage, float floor) {
-    constexpr int RL = W + 1;
-    auto issue = [&](int j) {
-        const int r0 = j * kChunk;
-        if (r0 < m) {
-            const int cnt = min(kChunk, m - r0) * RL;
-            float *dst = stage + (j & 1) * kChunk * RL;
+    constexpr int RL = W + 1, CH = RL * RL;
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < m) {  // rows r0 .. r0 + W < n: inside the block's band
+            float *dst = stage + (per & 1) * CH * 32;
             const float *src = band + (int64_t)r0 * RL;
-            for (int i = 0; i < cnt; ++i) cp_async4(dst + i, src + i);
+#pragma unroll
+            for (int i = 0; i < CH; ++i) cp_async4(dst + i * 32, src + i);
         }
         cp_async_commit();
     };
-    issue(0);
     issue(1);
-    float Wn[W + 1][W + 1];
-    float od[W + 1];  // original diagonal of the window rows
+    float Wn[RL][RL];  // [row slot][column slot]
+    float od[RL];      // original diagonal per row slot
 #pragma unroll
     for (int r = 0; r <= W; ++r) {
 #pragma unroll
         for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[(int64_t)r * RL + (r - c)] : 0.0f;
         od[r] = Wn[r][r];
     }
-    cp_async_wait<1>();
-    int next = 2;
-    for (int k = 0; k < m; ++k) {
-        const float d = Wn[0][0];
-        if (!(d > floor * od[0])) {  // includes d <= 0: FP64 decides
-            cp_async_wait<0>();
-            return kRescue;
-        }
+    // One elimination step at phase PH (k = p RL + PH).  lrow = band row
+    // p RL; src = the staged rows of period p + 1.  Rows >= m only ever feed
+    // rows >= m, which nothing reads, so they need no masking; GUARD stops
+    // the steps k >= m of the last, partial period.
+    bool bad = false;
+    auto step = [&](auto PHc, float *lrow, const float *src, bool live) {
+        constexpr int PH = decltype(PHc)::value;
+        if (!live) return;
+        const float d = Wn[PH][PH];
+        bad |= !(d > floor * od[PH]);  // includes d <= 0 and NaN
         const float rs = rsqrtf(d);
-        band[(int64_t)k * RL] = d * rs;
-        float l[W + 1];
+        lrow[PH * RL] = d * rs;
+        float l[RL];
 #pragma unroll
         for (int r = 1; r <= W; ++r) {
-            l[r] = k + r < m ? Wn[r][0] * rs : 0.0f;
-            if (k + r < m) band[(int64_t)(k + r) * RL + r] = l[r];
+            l[r] = Wn[(PH + r) % RL][PH] * rs;
+            lrow[(PH + r) * RL + r] = l[r];
         }
+        // the next pivot first, so its rsqrt can start early
+        if constexpr (W >= 1) Wn[(PH + 1) % RL][(PH + 1) % RL] = fmaf(-l[1], l[1], Wn[(PH + 1) % RL][(PH + 1) % RL]);
 #pragma unroll
         for (int r = 1; r <= W; ++r)
 #pragma unroll
-            for (int c = 1; c <= r; ++c) Wn[r][c] = fmaf(-l[r], l[c], Wn[r][c]);
+            for (int c = 1; c <= r; ++c)
+                if (r > 1 || c > 1) Wn[(PH + r) % RL][(PH + c) % RL] = fmaf(-l[r], l[c], Wn[(PH + r) % RL][(PH + c) % RL]);
+        // row k+1+W enters slot PH at columns k+1 .. k+1+W
 #pragma unroll
-        for (int r = 0; r < W; ++r)
-#pragma unroll
-            for (int c = 0; c <= r; ++c) Wn[r][c] = Wn[r + 1][c + 1];
-        const int R = k + 1 + W;  // row entering the window
-        if (R < m && R % kChunk == 0) {
-            if (R / kChunk + 1 >= next) {
-                issue(next);
-                ++next;
-            }
-            cp_async_wait<1>();
+        for (int c = 0; c <= W; ++c) Wn[PH][(PH + 1 + c) % RL] = src[(PH * RL + (W - c)) * 32];
+        od[PH] = Wn[PH][PH];
+    };
+    const int P = m / RL;  // full periods
+    for (int p = 0; p <= P; ++p) {
+        issue(p + 2);
+        cp_async_wait<1>();  // period p + 1 has landed
+        const float *src = stage + ((p + 1) & 1) * CH * 32;
+        float *lrow = band + (int64_t)p * RL * RL;
+        if (p < P) {
+            auto full = [&](auto PHc) { step(PHc, lrow, src, true); };
+            StaticFor<0, RL>::run(full);
+        } else {
+            const int left = m - p * RL;  // steps of the last, partial period
+            auto part = [&](auto PHc) { step(PHc, lrow, src, decltype(PHc)::value < left); };
+            StaticFor<0, RL>::run(part);
         }
-        const float *row = stage + ((R / kChunk) & 1) * kChunk * RL + (R % kChunk) * RL;
-#pragma unroll
-        for (int c = 0; c <= W; ++c) Wn[W][c] = R < m ? row[W - c] : 0.0f;
-#pragma unroll
-        for (int r = 0; r < W; ++r) od[r] = od[r + 1];
-        od[W] = Wn[W][W];
+        if (bad) break;
     }
     cp_async_wait<0>();
-    return 0;
+    return bad ? kRescue : 0;
 }
 
 template <int W>
@@ -731,6 +767,8 @@ struct F32BandDispatch<0> {
     }
 };
 
+constexpr int kF32BandStage = 2 * 17 * 17 * 32;  // floats: two periods of W = 16, 32 lanes
+
 // One CTA per F32Cta slice: 32 lanes for W <= 8, 16 lanes above.
 __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Cta *__restrict__ ctas,
                                                       const int32_t *__restrict__ items,
@@ -741,8 +779,7 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Cta *__restrict__
     if ((int)threadIdx.x >= c.count) return;
     const int bi = items[c.first + threadIdx.x];
     const BlockDesc bd = blocks[bi];
-    float *stage = fsm + threadIdx.x * (2 * kChunk * (c.w + 1) + 1);
-    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, stage, floor);
+    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, fsm + threadIdx.x, floor);
 }
 
 // Border pass, G2 lanes (one per border row) per block, exact width W.
@@ -1266,7 +1303,8 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
         const int nf = (int)pl->f32_items.size();
         if (nf) {
             k_f32_shadow_in<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow.p);
-            const size_t smem = (size_t)32 * (2 * kChunk * 9 + 1) * sizeof(float);
+            const size_t smem = (size_t)kF32BandStage * sizeof(float);
+            cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_f32_band_pass<<<(unsigned)pl->f32_band_ctas.size(), 32, smem, st>>>(
                 (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info,
                 (float)pl->fp32_pivot_floor);

@@ -417,23 +417,25 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
     if (sample) *sample = s;
+    // mirrors the launch sequence of sympix_factor_blocks
     int f = 0;
-    const bool band = !(pl->factor_items[0].empty() && pl->factor_items[1].empty() && pl->factor_items[2].empty());
-    if (factor_precision == SYMPIX_PREC_FP32 && storage == SYMPIX_STORE_PBAND) {
-        // shadow copy, band and border passes, and the FP64 rescue launches
-        // (which return at once for blocks that need no rescue)
-        f = pl->f32_items.empty() ? 0 : 3;
-        if (band) {
-            f += 2;
-            for (int l = 1; l <= 2; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    const bool pband = storage == SYMPIX_STORE_PBAND;
+    const bool l0 = !pl->factor_items[0].empty(), l1 = !pl->factor_items[1].empty(),
+               l2 = !pl->factor_items[2].empty();
+    if (factor_precision == SYMPIX_PREC_FP32 && pband) {
+        if (!pl->f32_items.empty()) {
+            // shadow in, band pass, shadow out, border pass, then the FP64
+            // rescue launches (which return at once for blocks that need none)
+            f = 3 + (pl->f32_border_ctas.empty() ? 0 : 1);
+            f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
         }
-    } else if (band) {
-        f = 2;
-        if (factor_precision != SYMPIX_PREC_FP32)
-            for (int l = 1; l <= 2; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
+    } else if (factor_precision == SYMPIX_PREC_FP32) {
+        f = (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
+    } else {
+        f = (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
     }
-    for (int l = 3; l < 6; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
-    if (factor_precision == SYMPIX_PREC_FP32 && !pl->factor_items[5].empty()) ++f;  // wide FP64 rescue
+    if (!pl->factor_items[5].empty()) f += (factor_precision == SYMPIX_PREC_FP32 && pband) ? 2 : 1;
+    for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
     if (factor) *factor = f;
     return SYMPIX_OK;
 }

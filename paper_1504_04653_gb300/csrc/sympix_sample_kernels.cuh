@@ -59,7 +59,7 @@ struct Arith<2> : ArF2 {
 // |s|, |s+d| <= K-1.  K is a template parameter: every index is static, the
 // kernel values and the N^-1 window sit in registers, one FMA per triple.
 template <class A, int WMAX, int K>
-__device__ __forceinline__ void same_count_entry(typename A::V (&acc)[WMAX + 1], int q, int n,
+__device__ __forceinline__ void same_count_entry(typename A::V (&acc)[WMAX + 1], int q, int n, int w,
                                                  const double *__restrict__ n64, const float *__restrict__ n32,
                                                  const float *__restrict__ nlo, int nstride,
                                                  const double *__restrict__ tb, const float *__restrict__ tb32,
@@ -79,6 +79,7 @@ __device__ __forceinline__ void same_count_entry(typename A::V (&acc)[WMAX + 1],
     }
 #pragma unroll
     for (int d = 0; d <= 2 * K - 2; ++d) {
+        if (d > w) break;  // offsets past the stored band (uniform per block)
 #pragma unroll
         for (int i = 0; i < 2 * K - 1; ++i) {
             const int a = i - (K - 1) + d;
@@ -89,19 +90,19 @@ __device__ __forceinline__ void same_count_entry(typename A::V (&acc)[WMAX + 1],
 
 template <class A, int WMAX, int K>
 struct SameCount {
-    __device__ static bool run(int Kr, typename A::V (&acc)[WMAX + 1], int q, int n, const double *n64,
+    __device__ static bool run(int Kr, typename A::V (&acc)[WMAX + 1], int q, int n, int w, const double *n64,
                                const float *n32, const float *nlo, int nstride, const double *tb, const float *tb32,
                                const float *tblo, int64_t tab) {
         if (Kr == K) {
-            same_count_entry<A, WMAX, K>(acc, q, n, n64, n32, nlo, nstride, tb, tb32, tblo, tab);
+            same_count_entry<A, WMAX, K>(acc, q, n, w, n64, n32, nlo, nstride, tb, tb32, tblo, tab);
             return true;
         }
-        return SameCount<A, WMAX, K - 1>::run(Kr, acc, q, n, n64, n32, nlo, nstride, tb, tb32, tblo, tab);
+        return SameCount<A, WMAX, K - 1>::run(Kr, acc, q, n, w, n64, n32, nlo, nstride, tb, tb32, tblo, tab);
     }
 };
 template <class A, int WMAX>
 struct SameCount<A, WMAX, 0> {
-    __device__ static bool run(int, typename A::V (&)[WMAX + 1], int, int, const double *, const float *,
+    __device__ static bool run(int, typename A::V (&)[WMAX + 1], int, int, int, const double *, const float *,
                                const float *, int, const double *, const float *, const float *, int64_t) {
         return false;
     }
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128) k_sample_pband(const SampleItem *__restri
             const int64_t tab = tbase + pe.tab;
             bool done = false;
             if (pe.P == 1 && pe.Q == 1)
-                done = SameCount<A, WMAX, KTOP>::run(pe.mmax / 2 + 1, acc, q, n, n64 + pe.noff, n32 + pe.noff,
+                done = SameCount<A, WMAX, KTOP>::run(pe.mmax / 2 + 1, acc, q, n, w, n64 + pe.noff, n32 + pe.noff,
                                                      nlo + pe.noff, pe.nstride, tb, tb32, tblo, tab);
             if (!done) general_entry<A, WMAX>(acc, q, w, pe, n64, n32, nlo, tb, tb32, tblo, tab);
         }

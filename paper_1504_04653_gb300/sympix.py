@@ -21,6 +21,7 @@ OPT_FP32_PIVOT_FLOOR = 1
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
+STAGE_TABLE, STAGE_SAMPLE, STAGE_FACTOR, STAGE_ALL = 1, 2, 4, 7
 BLOCK_PBAND, BLOCK_DENSE = 0, 1
 
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp32x2": PREC_FP32X2}
@@ -65,6 +66,10 @@ SIGNATURES = [
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
     ("sympix_factor_blocks", _i, [_vp, _i, _i, _vp, _vp, _vp]),
     ("sympix_plan_free", None, [_vp]),
+    ("sympix_step_create", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("sympix_step_launch", _i, [_vp, _i, _vp]),
+    ("sympix_step_kernels", _i, [_vp, _i, _i64p]),
+    ("sympix_step_free", None, [_vp]),
     ("sympix_last_error", ctypes.c_char_p, []),
     ("sympix_version", ctypes.c_char_p, []),
 ]
@@ -263,6 +268,53 @@ def sympix_factor_blocks(plan: Plan, blocks, storage="pband", precision="fp64", 
     _check(lib().sympix_factor_blocks(plan.handle, STORAGES[storage], PRECISIONS[precision], _ptr(blocks),
                                       _ptr(info), _stream(stream)))
     return info
+
+
+class Step:
+    """The kernel-table, sampling and factor calls captured as CUDA graphs
+    (sympix_step_create); launch() replays them.  The graphs keep the tensors'
+    addresses: update bl, dl and ninv in place between launches.  The step
+    holds references to every tensor it captured."""
+
+    def __init__(self, plan: Plan, bl, dl, ninv, blocks, info, storage="pband", sample_precision="fp32",
+                 factor_precision="fp32"):
+        import torch
+        L1 = plan.grid.lmax + 1
+        for t in (bl, dl):
+            if t.dtype != torch.float64 or tuple(t.shape) != (plan.nops, L1):
+                raise SympixError(EINVAL, f"coefficients must be float64 [{plan.nops}, {L1}]")
+        if ninv.dtype != torch.float64 or tuple(ninv.shape) != (plan.nops, plan.grid.npix):
+            raise SympixError(EINVAL, f"ninv must be float64 [{plan.nops}, {plan.grid.npix}]")
+        nbytes, _ = plan.blocks_size(storage)
+        if blocks.dtype != torch.float64 or blocks.numel() * 8 < nbytes:
+            raise SympixError(EINVAL, "blocks buffer too small")
+        if info.dtype != torch.int32 or info.numel() < plan.nblocks:
+            raise SympixError(EINVAL, f"info must be int32 [{plan.nblocks}]")
+        self.plan, self._keep = plan, (bl, dl, ninv, blocks, info)
+        h = _vp()
+        _check(lib().sympix_step_create(plan.handle, _ptr(bl), _ptr(dl), _ptr(ninv), STORAGES[storage],
+                                        PRECISIONS[sample_precision], PRECISIONS[factor_precision], _ptr(blocks),
+                                        _ptr(info), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stages=STAGE_ALL, stream=None):
+        _check(lib().sympix_step_launch(self._h, int(stages), _stream(stream)))
+
+    def kernels(self, stages=STAGE_ALL) -> int:
+        c = ctypes.c_int64()
+        _check(lib().sympix_step_kernels(self._h, int(stages), ctypes.byref(c)))
+        return c.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.sympix_step_free(h)
+            self._h = None
+
+
+def sympix_step_create(plan: Plan, bl, dl, ninv, blocks, info, storage="pband", sample_precision="fp32",
+                       factor_precision="fp32") -> Step:
+    return Step(plan, bl, dl, ninv, blocks, info, storage, sample_precision, factor_precision)
 
 
 # -- host-side views of the block buffer (for tests and users) -----------------------

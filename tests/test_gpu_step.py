@@ -1,0 +1,103 @@
+"""Captured step (sympix_step_create / sympix_step_launch) against direct calls.
+
+The graphs replay the same kernels on the same inputs, so the blocks, the
+factors and the info codes must agree bit for bit with the direct calls.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1504_04653_gb300 import sympix as S  # noqa: E402
+from paper_1504_04653_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(name, seeds=None):
+    wl = W.WORKLOADS[name]
+    if seeds is not None:
+        wl = W.Workload(wl.name, wl.lmax, wl.fwhm_arcmin, wl.band_deg, seeds, wl.desc)
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    dev = torch.device("cuda", 0)
+    bl = torch.tensor(wl.beams(), dtype=torch.float64, device=dev)
+    dl = torch.tensor(wl.priors(), dtype=torch.float64, device=dev)
+    ninv = torch.tensor(wl.ninv(colat), dtype=torch.float64, device=dev)
+    return wl, grid, plan, colat, bl, dl, ninv
+
+
+def _direct(plan, bl, dl, ninv, storage, sprec, fprec):
+    # sampling leaves the border rows of a periodic-band block unwritten (the
+    # factor fills them): start from zeros on both sides
+    nbytes, _ = plan.blocks_size(storage)
+    blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
+    S.sympix_kernel_table(plan, bl, dl)
+    S.sympix_sample_blocks(plan, ninv, precision=sprec, storage=storage, out=blocks)
+    sampled = blocks.clone()
+    info = S.sympix_factor_blocks(plan, blocks, storage=storage, precision=fprec)
+    torch.cuda.synchronize()
+    return sampled.cpu().numpy(), blocks.cpu().numpy(), info.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,storage,sprec,fprec", [
+    ("lmax500", "pband", "fp32", "fp32"),
+    ("lmax500", "pband", "fp64", "fp64"),
+    ("lmax64", "dense", "fp32x2", "fp32x2"),
+])
+def test_step_matches_direct_calls(name, storage, sprec, fprec):
+    wl, grid, plan, colat, bl, dl, ninv = _setup(name)
+    s_ref, f_ref, i_ref = _direct(plan, bl, dl, ninv, storage, sprec, fprec)
+    nbytes, _ = plan.blocks_size(storage)
+    blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
+    info = torch.full((plan.nblocks,), -7, dtype=torch.int32, device="cuda")
+    step = S.Step(plan, bl, dl, ninv, blocks, info, storage, sprec, fprec)
+    assert step.kernels() == sum(plan.launches(storage, sprec, fprec))
+    assert step.kernels(S.STAGE_TABLE) == plan.launches(storage, sprec, fprec)[0]
+    step.launch(S.STAGE_TABLE | S.STAGE_SAMPLE)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocks.cpu().numpy(), s_ref)
+    step.launch(S.STAGE_FACTOR)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocks.cpu().numpy(), f_ref)
+    assert np.array_equal(info.cpu().numpy(), i_ref)
+    # a second replay of the whole step on another stream gives the same
+    st = torch.cuda.Stream()
+    blocks.zero_()
+    step.launch(S.STAGE_ALL, stream=st)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocks.cpu().numpy(), f_ref)
+
+
+def test_step_reads_inputs_at_replay():
+    """Updating N^-1 in place and replaying sampling + factor gives what
+    direct calls on the new N^-1 give."""
+    wl, grid, plan, colat, bl, dl, ninv = _setup("lmax500")
+    nbytes, _ = plan.blocks_size("pband")
+    blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
+    info = torch.empty(plan.nblocks, dtype=torch.int32, device="cuda")
+    step = S.Step(plan, bl, dl, ninv, blocks, info, "pband", "fp32", "fp32")
+    step.launch()
+    wl2 = W.Workload(wl.name, wl.lmax, wl.fwhm_arcmin, wl.band_deg, [s + 17 for s in wl.seeds], wl.desc)
+    ninv.copy_(torch.tensor(wl2.ninv(colat), dtype=torch.float64, device="cuda"))
+    blocks.zero_()
+    step.launch(S.STAGE_SAMPLE | S.STAGE_FACTOR)
+    torch.cuda.synchronize()
+    got_b, got_i = blocks.cpu().numpy(), info.cpu().numpy()
+    _, f_ref, i_ref = _direct(plan, bl, dl, ninv, "pband", "fp32", "fp32")
+    assert np.array_equal(got_b, f_ref)
+    assert np.array_equal(got_i, i_ref)
+
+
+def test_step_rejects_bad_arguments():
+    wl, grid, plan, colat, bl, dl, ninv = _setup("lmax64")
+    nbytes, _ = plan.blocks_size("pband")
+    blocks = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+    info = torch.empty(plan.nblocks, dtype=torch.int32, device="cuda")
+    step = S.Step(plan, bl, dl, ninv, blocks, info)
+    for bad in (0, 8, -1):
+        with pytest.raises(S.SympixError):
+            step.launch(bad)
+    with pytest.raises(S.SympixError):
+        S.Step(plan, bl, dl, ninv, blocks[:10], info)
