@@ -594,59 +594,69 @@ __global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int 
 // ---------------------------------------------------------------------------
 // FP32 factorisation on a shadow of the band.
 //
-// The band rows are converted once to an FP32 copy (coalesced), the band
-// pass eliminates on that copy, the L11 rows are converted back once, and
-// the border pass reads the FP32 rows; no conversion sits inside the
-// elimination loops.  Kernels are specialised on the exact band width W
-// (a CTA only holds blocks of one width), so every window index is static.
+// Blocks of one exact width W <= 16 are factored in slices of up to 32.  A
+// slice's band rows are converted once to an FP32 copy (the shadow) laid out
+// lane-interleaved: element e (row e / (W+1), offset e % (W+1)) of the
+// slice's block L sits at 32 e + L.  With one lane per block every warp
+// access of the band pass then covers 32 consecutive floats, and the
+// border pass stages the rows of all 32 blocks with contiguous copies.
+//   1. k_f32_shadow_in   FP64 rows -> interleaved FP32 (a shared-memory
+//                        transpose, coalesced on both sides);
+//   2. k_f32_band_pass   A11 = L11 L11^T, one lane per block;
+//   3. k_f32_border_pass L21 = A21 L11^-T into an interleaved FP32 buffer,
+//                        S = L21 L21^T and the corner A22 - S = L22 L22^T;
+//   4. k_f32_out         L11 and L21 back to the FP64 blocks.
+// Kernels are specialised on W (a slice holds one width), so every window
+// index is static.
 // ---------------------------------------------------------------------------
-
-// One CTA-sized slice of a width class: blocks items[first .. first+count).
-struct F32Cta {
-    int32_t w, first, count, pad;
-};
-
-__global__ void k_f32_shadow_in(const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
-                                const double *__restrict__ out, float *__restrict__ sh) {
-    const BlockDesc bd = blocks[items[blockIdx.x]];
-    const int64_t cnt = (int64_t)bd.n * (bd.w + 1);
-    const double *src = out + bd.off_pband;
-    float *dst = sh + bd.off_pband;
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = f64_to_f32_bits(src[i]);
-}
-
-// L11 rows (row < m, entries d <= row) back to the FP64 blocks.  The band is
-// one contiguous run of m (w+1) values: thread t copies elements t, t + T,
-// t + 2T, ..., tracking (row, offset) by constant strides, so consecutive
-// threads touch consecutive addresses.
-__global__ void __launch_bounds__(256) k_f32_shadow_out(const int32_t *__restrict__ items,
-                                                        const BlockDesc *__restrict__ blocks,
-                                                        const int32_t *__restrict__ info,
-                                                        const float *__restrict__ sh, double *__restrict__ out) {
-    const int bi = items[blockIdx.x];
-    if (info[bi] != 0) return;
-    const BlockDesc bd = blocks[bi];
-    const int RL = bd.w + 1, m = bd.n - bd.w;
-    const int64_t cnt = (int64_t)m * RL;
-    const float *src = sh + bd.off_pband;
-    double *dst = out + bd.off_pband;
-    const int T = blockDim.x;
-    const int drow = T / RL, dd = T % RL;
-    int row = threadIdx.x / RL, d = threadIdx.x % RL;
-    for (int64_t e = threadIdx.x; e < cnt; e += T) {
-        if (d <= row) dst[e] = f32_to_f64_bits(src[e]);
-        row += drow;
-        d += dd;
-        if (d >= RL) {
-            d -= RL;
-            ++row;
-        }
-    }
-}
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// One CTA per 64 elements x 32 blocks of a slice.
+__global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ tiles,
+                                                       const F32Slice *__restrict__ slices,
+                                                       const int32_t *__restrict__ items,
+                                                       const BlockDesc *__restrict__ blocks,
+                                                       const double *__restrict__ out, float *__restrict__ sh) {
+    __shared__ float tile[64][33];
+    __shared__ int64_t s_off[32];
+    __shared__ int s_cnt[32];
+    const int2 tl = tiles[blockIdx.x];
+    const F32Slice sl = slices[tl.x];
+    const int RL = sl.w + 1, e0 = tl.y;
+    if (threadIdx.x < 32) {
+        int64_t off = 0;
+        int cnt = 0;
+        if ((int)threadIdx.x < sl.count) {
+            const BlockDesc bd = blocks[items[sl.first + threadIdx.x]];
+            off = bd.off_pband;
+            cnt = bd.n * RL;
+        }
+        s_off[threadIdx.x] = off;
+        s_cnt[threadIdx.x] = cnt;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+        const int L = i >> 6, e = i & 63;
+        float v = 0.0f;
+        if (e0 + e < s_cnt[L]) v = f64_to_f32_bits(out[s_off[L] + e0 + e]);
+        tile[e][L] = v;
+    }
+    __syncthreads();
+    const int lim = sl.rows * RL;
+    float *dst = sh + sl.sh + (int64_t)e0 * 32;
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+        const int e = i >> 5, L = i & 31;
+        if (e0 + e < lim) dst[e * 32 + L] = tile[e][L];
+    }
 }
 
 // f(integral_constant<int, I>) for I = B .. E-1, expanded at compile time.
@@ -664,7 +674,7 @@ struct StaticFor<E, E> {
     __device__ __forceinline__ static void run(F &) {}
 };
 
-// Band pass on the FP32 shadow, one lane per block, exact width W.
+// Band pass of one block in one lane, exact width W.
 //
 // The active window is the lower triangle of rows k..k+W at columns k..k+r
 // (row k+r).  Row i and column j are kept in register slot i mod (W+1) and
@@ -672,25 +682,26 @@ struct StaticFor<E, E> {
 // so every slot index is static and moving the window costs nothing: the
 // row retiring at step k frees the slot the row k+1+W enters.  During
 // period p (steps k = p(W+1) .. p(W+1)+W) the entering rows are exactly the
-// W+1 rows of period p+1, staged into shared memory with cp.async one
-// period ahead.  Inside a period the code is straight-line, so the
-// scheduler overlaps the next pivot's rsqrt with the rest of the update.
-// Pivots are checked against the floor once per period: a block that fell
-// below it is recomputed from its FP64 input anyway.
+// W+1 rows of period p+1, which the warp stages into shared memory one
+// period ahead with contiguous 16-byte copies.  Inside a period the code is
+// straight-line, so the scheduler overlaps the next pivot's rsqrt with the
+// rest of the update.  Pivots are checked against the floor as they come;
+// a block that fell below it stops and is recomputed from its FP64 input.
 //
-// band: the block's shadow rows (row i at band + i (W+1), entry d = column
-// i - d); stage: this lane's two period buffers, lane-interleaved (element
-// e at stage[32 e]) so that the lanes' loads hit distinct banks.
+// shs: the slice's interleaved shadow; m: this lane's A11 size (0 for an
+// idle lane); mmax: the slice's largest m (every lane runs mmax's periods,
+// so that all take part in the staging); stage: the CTA's two period
+// buffers, laid out like the shadow.
 template <int W>
-__device__ __forceinline__ int f32_band(float *band, int m, float *stage, float floor) {
+__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor) {
     constexpr int RL = W + 1, CH = RL * RL;
+    float *band = shs + lane;  // element e at band[32 e]
     auto issue = [&](int per) {
         const int r0 = per * RL;
-        if (r0 < m) {  // rows r0 .. r0 + W < n: inside the block's band
+        if (r0 < mmax) {  // rows r0 .. r0 + W < the slice's rows
             float *dst = stage + (per & 1) * CH * 32;
-            const float *src = band + (int64_t)r0 * RL;
-#pragma unroll
-            for (int i = 0; i < CH; ++i) cp_async4(dst + i * 32, src + i);
+            const float *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = lane; i < CH * 8; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
         }
         cp_async_commit();
     };
@@ -700,29 +711,33 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage, float 
 #pragma unroll
     for (int r = 0; r <= W; ++r) {
 #pragma unroll
-        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[(int64_t)r * RL + (r - c)] : 0.0f;
+        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[((int64_t)r * RL + (r - c)) * 32] : 0.0f;
         od[r] = Wn[r][r];
     }
     // One elimination step at phase PH (k = p RL + PH).  lrow = band row
-    // p RL; src = the staged rows of period p + 1.  Rows >= m only ever feed
-    // rows >= m, which nothing reads, so they need no masking; GUARD stops
-    // the steps k >= m of the last, partial period.
-    bool bad = false;
-    auto step = [&](auto PHc, float *lrow, const float *src, bool live) {
+    // p RL; src = this lane's staged rows of period p + 1.  Rows >= m only
+    // ever feed rows >= m, which nothing reads, so they need no masking.
+    // The pivot d of row k and rs = 1/sqrt(d) arrive from the previous
+    // step: each step forms the next pivot first (one product) and starts
+    // its rsqrt before the rest of the update.
+    bool bad = !(Wn[0][0] > floor * od[0]);
+    float d = Wn[0][0], rs = rsqrtf(Wn[0][0]);
+    auto step = [&](auto PHc, float *lrow, const float *src, bool live, int kbase) {
         constexpr int PH = decltype(PHc)::value;
+        constexpr int P1 = (PH + 1) % RL;
         if (!live) return;
-        const float d = Wn[PH][PH];
-        bad |= !(d > floor * od[PH]);  // includes d <= 0 and NaN
-        const float rs = rsqrtf(d);
-        lrow[PH * RL] = d * rs;
+        lrow[PH * RL * 32] = d * rs;
         float l[RL];
-#pragma unroll
-        for (int r = 1; r <= W; ++r) {
-            l[r] = Wn[(PH + r) % RL][PH] * rs;
-            lrow[(PH + r) * RL + r] = l[r];
+        float dn = 0.0f, rsn = 0.0f;
+        if constexpr (W >= 1) {
+            l[1] = Wn[P1][PH] * rs;
+            dn = fmaf(-l[1], l[1], Wn[P1][P1]);
+            rsn = rsqrtf(dn);
         }
-        // the next pivot first, so its rsqrt can start early
-        if constexpr (W >= 1) Wn[(PH + 1) % RL][(PH + 1) % RL] = fmaf(-l[1], l[1], Wn[(PH + 1) % RL][(PH + 1) % RL]);
+#pragma unroll
+        for (int r = 2; r <= W; ++r) l[r] = Wn[(PH + r) % RL][PH] * rs;
+#pragma unroll
+        for (int r = 1; r <= W; ++r) lrow[((PH + r) * RL + r) * 32] = l[r];
 #pragma unroll
         for (int r = 1; r <= W; ++r)
 #pragma unroll
@@ -732,22 +747,36 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage, float 
 #pragma unroll
         for (int c = 0; c <= W; ++c) Wn[PH][(PH + 1 + c) % RL] = src[(PH * RL + (W - c)) * 32];
         od[PH] = Wn[PH][PH];
+        if constexpr (W >= 1) {
+            d = dn;
+            rs = rsn;
+        } else {  // a diagonal block: the next pivot is the entering row's
+            (void)dn;
+            (void)rsn;
+            d = Wn[0][0];
+            rs = rsqrtf(d);
+        }
+        // the next pivot (rows >= m are not A11's); includes d <= 0 and NaN
+        bad |= kbase + PH + 1 < m && !(d > floor * od[P1]);
     };
-    const int P = m / RL;  // full periods
-    for (int p = 0; p <= P; ++p) {
+    const int PW = mmax / RL;  // the slice's last period
+    for (int p = 0; p <= PW; ++p) {
         issue(p + 2);
         cp_async_wait<1>();  // period p + 1 has landed
-        const float *src = stage + ((p + 1) & 1) * CH * 32;
-        float *lrow = band + (int64_t)p * RL * RL;
-        if (p < P) {
-            auto full = [&](auto PHc) { step(PHc, lrow, src, true); };
+        __syncwarp();        // ... for every lane's copies
+        const float *src = stage + ((p + 1) & 1) * CH * 32 + lane;
+        float *lrow = band + (int64_t)p * RL * RL * 32;
+        const int left = m - p * RL;  // this lane's steps left
+        const int kbase = p * RL;
+        if (left >= RL) {
+            auto full = [&](auto PHc) { step(PHc, lrow, src, true, kbase); };
             StaticFor<0, RL>::run(full);
-        } else {
-            const int left = m - p * RL;  // steps of the last, partial period
-            auto part = [&](auto PHc) { step(PHc, lrow, src, decltype(PHc)::value < left); };
+        } else if (left > 0) {
+            auto part = [&](auto PHc) { step(PHc, lrow, src, decltype(PHc)::value < left, kbase); };
             StaticFor<0, RL>::run(part);
         }
-        if (bad) break;
+        if (bad) m = 0;  // stop this lane; the warp keeps staging
+        __syncwarp();    // every lane is done with the buffer the next copies overwrite
     }
     cp_async_wait<0>();
     return bad ? kRescue : 0;
@@ -755,183 +784,341 @@ __device__ __forceinline__ int f32_band(float *band, int m, float *stage, float 
 
 template <int W>
 struct F32BandDispatch {
-    __device__ static int run(int w, float *band, int m, float *stage, float floor) {
-        if (w == W) return f32_band<W>(band, m, stage, floor);
-        return F32BandDispatch<W - 1>::run(w, band, m, stage, floor);
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor) {
+        if (w == W) return f32_band<W>(shs, lane, m, mmax, stage, floor);
+        return F32BandDispatch<W - 1>::run(w, shs, lane, m, mmax, stage, floor);
     }
 };
 template <>
 struct F32BandDispatch<0> {
-    __device__ static int run(int w, float *band, int m, float *stage, float floor) {
-        return w == 0 ? f32_band<0>(band, m, stage, floor) : -1;
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor) {
+        return w == 0 ? f32_band<0>(shs, lane, m, mmax, stage, floor) : -1;
     }
 };
 
 constexpr int kF32BandStage = 2 * 17 * 17 * 32;  // floats: two periods of W = 16, 32 lanes
 
-// One CTA per F32Cta slice: 32 lanes for W <= 8, 16 lanes above.
-__global__ void __launch_bounds__(32) k_f32_band_pass(const F32Cta *__restrict__ ctas,
+// One warp per slice, one lane per block.
+__global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict__ slices,
                                                       const int32_t *__restrict__ items,
                                                       const BlockDesc *__restrict__ blocks, float *__restrict__ sh,
                                                       int32_t *__restrict__ info, float floor) {
-    extern __shared__ float fsm[];
-    const F32Cta c = ctas[blockIdx.x];
-    if ((int)threadIdx.x >= c.count) return;
-    const int bi = items[c.first + threadIdx.x];
-    const BlockDesc bd = blocks[bi];
-    info[bi] = F32BandDispatch<16>::run(bd.w, sh + bd.off_pband, bd.n - bd.w, fsm + threadIdx.x, floor);
+    extern __shared__ __align__(16) float fsm[];
+    const F32Slice sl = slices[blockIdx.x];
+    const int lane = threadIdx.x;
+    int m = 0, bi = -1;
+    if (lane < sl.count) {
+        bi = items[sl.first + lane];
+        m = blocks[bi].n - sl.w;
+    }
+    const int r = F32BandDispatch<16>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, fsm, floor);
+    if (bi >= 0) info[bi] = r;
 }
 
-// Border pass, G2 lanes (one per border row) per block, exact width W.
-// The group stages the block's FP32 L11 rows; every lane reads the whole
-// band row k from shared memory (broadcast), forms its L[m+b][k], and
-// accumulates the corner row S[b][.]; one lane factors the W x W corner.
-template <int W, int G2>
-__device__ __forceinline__ void f32_border(const BlockDesc &bd, const float *__restrict__ sband, double *__restrict__ out,
-                                           int t, unsigned gmask, float *stage, int32_t *info_bi) {
-    constexpr int RL = W + 1;
-    const int n = bd.n, m = n - W;
-    const PBandView v{out + bd.off_pband, out + bd.off_pband + (int64_t)n * RL, n, W, m};
-    const int b = t;
-    const bool used = b < W;
-    auto issue = [&](int j) {
-        const int r0 = j * kChunk;
-        if (r0 < m) {
-            const int cnt = min(kChunk, m - r0) * RL;
-            float *dst = stage + (j & 1) * kChunk * RL;
-            const float *src = sband + (int64_t)r0 * RL;
-            for (int i = t; i < cnt; i += G2) cp_async4(dst + i, src + i);
+// Border pass of one slice, exact width W: the forward substitution
+// L21 = A21 L11^-T,
+//   L21[b][k] = (A21[b][k] - sum_c L21[b][k-W+c] L11[k][k-W+c]) / L11[k][k],
+// with A21 zero except in its first W columns (the wrap) and its last W.
+// One CTA per slice; lane = block, warp q owns border rows R q .. R q + R-1
+// of all 32 blocks (R = 1 for W <= 8, 2 above).  Like the band pass it
+// walks the columns by periods of W+1 with the L11 rows staged one period
+// ahead, and keeps each row's last W values in register slot
+// (column mod W+1), so every index is static.  L21 goes to the
+// lane-interleaved FP32 border buffer (element (b, k) of block L at
+// 32 (b kc + k) + L, kc = the slice's largest m) and, a period at a time,
+// through shared memory to the corner sums S = L21 L21^T, which the 8 warps
+// share pair by pair.  At the end one thread per block factors its corner
+// A22 - S = L22 L22^T in FP64.
+constexpr int kBorderThreads = 256;
+
+template <int W>
+__device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
+                                           const double *__restrict__ out, const int64_t *s_off, const int *s_n,
+                                           const int *s_live, float *stage, int *binfo) {
+    constexpr int RL = W + 1, CH = RL * RL;
+    constexpr int R = (W + 7) / 8;  // border rows per lane
+    const int lane = threadIdx.x & 31, b0 = (threadIdx.x >> 5) * R;
+    const bool rows = b0 < W;       // warp-uniform: this warp owns border rows
+    const int n = s_n[lane], m = n - W;
+    const bool live = s_live[lane];
+    const PBandView view{const_cast<double *>(out) + s_off[lane],
+                         const_cast<double *>(out) + s_off[lane] + (int64_t)n * RL, n, W, m};
+    const int kc = sl.rows - W;
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
+            float *dst = stage + (per % 3) * CH * 32;
+            const float *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = threadIdx.x; i < CH * 8; i += kBorderThreads) cp_async16(dst + 4 * i, src + 4 * i);
         }
         cp_async_commit();
     };
-    issue(0);
-    issue(1);
-    int next = 2;
-    float y[W];
-    float sacc[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-        y[c] = 0.0f;
-        sacc[c] = 0.0f;
+    float *vbuf = stage + 3 * CH * 32;  // two periods of L21 values, [b][column][lane]
+    float *vb = vbuf;                   // the current period's
+    float *abuf = vbuf + 2 * W * RL * 32;  // A21 at the last W columns, [b][c][lane]: A[m+b][m-W+c]
+    for (int i = threadIdx.x; i < W * W * 32; i += kBorderThreads) {
+        const int L = i & 31, bc = i >> 5, bb = bc / (W > 0 ? W : 1), c = bc - bb * W;
+        float v = 0.0f;
+        if (s_live[L]) {
+            const int nL = s_n[L], mL = nL - W;
+            double *o = const_cast<double *>(out) + s_off[L];
+            const PBandView vL{o, o + (int64_t)nL * RL, nL, W, mL};
+            v = f64_to_f32_bits(vL.a(mL + bb, mL - W + c));
+        }
+        abuf[i] = v;
     }
-    // A21 is nonzero only in the first W columns (wrap) and the last W
-    // (band); in between the substitution only propagates what the wrap
-    // part started, which decays geometrically.  Once every lane's window
-    // holds exact FP32 zeros each further column is exactly zero, so the
-    // group jumps to the band part and writes the zeros directly.
-    const int kband = ((m - W) / kChunk) * kChunk;  // chunk-aligned, <= first band-part column
-    for (int k = 0; k < m; ++k) {
-        if (k % kChunk == 0) {
-            if (k > W && k < kband) {
-                bool zero = true;
+    float aw[R][W];  // A21 of my rows at columns < W (the wrap part)
+    float y[R][RL];  // L21 of my rows at the last W columns, slot = column mod RL
 #pragma unroll
-                for (int c = 0; c < W; ++c) zero = zero && (y[c] == 0.0f);
-                if (__all_sync(gmask, zero)) {
-                    if (used)
-                        for (int kk = k; kk < kband; ++kk) v.put_b(b, kk, 0.0);
-                    k = kband;
-                    cp_async_wait<0>();
-                    __syncwarp(gmask);
-                    issue(k / kChunk);
-                    issue(k / kChunk + 1);
-                    next = k / kChunk + 2;
-                }
-            }
-            if (k / kChunk + 1 >= next) {
-                issue(next);
-                ++next;
-            }
-            cp_async_wait<1>();
-            __syncwarp(gmask);
-        }
-        const float *row = stage + ((k / kChunk) & 1) * kChunk * RL + (k % kChunk) * RL;
-        // L[k][k-W+c] = row[W-c]; entries left of column 0 are zero
-        float acc = 0.0f;
-        if (used && (k <= b || k >= m + b - W)) acc = f64_to_f32_bits(v.a(m + b, k));
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            const float lc = k - W + c >= 0 ? row[W - c] : 0.0f;
-            acc = fmaf(-y[c], lc, acc);
-        }
-        const float rd = rsqrtf(row[0]);
-        const float val = used ? acc * (rd * rd) : 0.0f;
-        if (used) v.put_b(b, k, f32_to_f64_bits(val));
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            const float vc = __shfl_sync(gmask, val, (threadIdx.x & 31) - t + c);
-            if (c <= b) sacc[c] = fmaf(val, vc, sacc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c + 1 < W; ++c) y[c] = y[c + 1];
-        y[W - 1] = val;
-        if ((k + 1) % kChunk == 0) __syncwarp(gmask);
-    }
-    cp_async_wait<0>();
-    if (used) {
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
         for (int c = 0; c < W; ++c)
-            if (c <= b) v.put_b(b, m + c, v.a(m + b, m + c) - f32_to_f64_bits(sacc[c]));
+            aw[r][c] = (rows && live && b0 + r < W) ? f64_to_f32_bits(view.a(m + b0 + r, c)) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < RL; ++c) y[r][c] = 0.0f;
     }
-    __syncwarp(gmask);
-    if (t == 0) {
+    // column k = p RL + PH; src = this lane's staged rows of period p
+    auto column = [&](auto PHc, auto FIRSTc, const float *src, int kbase) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr bool FIRST = decltype(FIRSTc)::value;  // p == 0: mask the columns left of 0
+        const int k = kbase + PH;
+        const float *row = src + PH * RL * 32;  // L11 row k: offset d at row[32 d]
+        float lr[RL];
+#pragma unroll
+        for (int d = 0; d < RL; ++d) lr[d] = row[d * 32];
+        const float rd = rsqrtf(lr[0]);
+        const float rcp = rd * rd;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int b = b0 + r;
+            float acc = 0.0f;
+            if constexpr (FIRST && PH < W) acc = aw[r][PH < W ? PH : 0];
+            {  // the last W columns, without a branch
+                const int c = k - (m - W);
+                const float a = abuf[((b < W ? b : W - 1) * W + min(max(c, 0), W - 1)) * 32 + lane];
+                acc = (c >= 0 && c < W) ? a : acc;
+            }
+#pragma unroll
+            for (int cc = 0; cc < W; ++cc) {
+                if (FIRST && PH - W + cc < 0) continue;  // left of column 0
+                acc = fmaf(-y[r][(PH - W + cc + RL) % RL], lr[W - cc], acc);
+            }
+            const float val = (live && b < W && k < m) ? acc * rcp : 0.0f;
+            y[r][PH] = val;
+            if (b < W) {
+                vb[(b * RL + PH) * 32 + lane] = val;
+                if (k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
+            }
+        }
+    };
+    // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b: the
+    // W (W+1)/2 pairs are dealt round-robin to the 8 warps, lane = block;
+    // each period's L21 values pass through vbuf
+    constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + 7) / 8;
+    const int wq = threadIdx.x >> 5;
+    int pb[NP > 0 ? NP : 1], pb2[NP > 0 ? NP : 1];
+    float sacc[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        int j = wq + 8 * i, bb = 0;
+        while (j > bb) {  // pair j = bb (bb+1)/2 + b2
+            j -= bb + 1;
+            ++bb;
+        }
+        pb[i] = bb < W ? bb : 0;
+        pb2[i] = bb < W ? j : 0;
+        sacc[i] = 0.0f;
+    }
+    auto accumulate = [&](const float *v) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            if (wq + 8 * i >= NPAIR) break;
+            const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+        }
+    };
+    issue(0);
+    issue(1);
+    const int PW = (kc - 1) / RL;  // the last period
+    for (int p = 0; p <= PW; ++p) {
+        cp_async_wait<1>();  // period p has landed
+        __syncthreads();     // ... for every thread's copies; period p-1's buffer is free
+        issue(p + 2);
+        if (p > 0) accumulate(vbuf + ((p - 1) & 1) * W * RL * 32);
+        vb = vbuf + (p & 1) * W * RL * 32;
+        if (rows) {
+            const float *src = stage + (p % 3) * CH * 32 + lane;
+            const int kbase = p * RL;
+            if (p == 0) {
+                auto f = [&](auto PHc) { column(PHc, std::true_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            } else {
+                auto f = [&](auto PHc) { column(PHc, std::false_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    accumulate(vbuf + (PW & 1) * W * RL * 32);
+    // the corner: sums to shared memory [block][b][b2], then one thread per
+    // block factors C = A22 - S = L22 L22^T in FP64
+    float *sS = stage;  // the staging is free now
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+        if (wq + 8 * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+    __syncthreads();
+    if (threadIdx.x < 32 && live) {
+        double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
+        double *outp = const_cast<double *>(out);
+        const PBandView v{outp + s_off[lane], outp + s_off[lane] + (int64_t)n * RL, n, W, m};
+        for (int i = 0; i < W; ++i)
+            for (int j = 0; j <= i; ++j) C[i * W + j] = v.a(m + i, m + j) - f32_to_f64_bits(sS[(lane * W + i) * W + j]);
         int inf = 0;
         for (int i = 0; i < W && inf == 0; ++i) {
             for (int j = 0; j <= i; ++j) {
-                double s = v.get_b(i, m + j);
-                for (int k = 0; k < j; ++k) s -= v.get_b(i, m + k) * v.get_b(j, m + k);
+                double sv = C[i * W + j];
+                for (int k = 0; k < j; ++k) sv -= C[i * W + k] * C[j * W + k];
                 if (j < i) {
-                    v.put_b(i, m + j, s / v.get_b(j, m + j));
+                    C[i * W + j] = sv / C[j * W + j];
                 } else {
-                    if (!(s > 0.0)) {
+                    if (!(sv > 0.0)) {
                         inf = m + i + 1;
                         break;
                     }
-                    v.put_b(i, m + i, sqrt(s));
+                    C[i * W + i] = sqrt(sv);
                 }
             }
         }
-        *info_bi = inf;
+        for (int i = 0; i < W; ++i)
+            for (int j = 0; j <= i; ++j) v.put_b(i, m + j, C[i * W + j]);
+        binfo[lane] = inf;
     }
 }
 
 template <int W>
 struct F32BorderDispatch {
-    __device__ static void run(int w, const BlockDesc &bd, const float *sband, double *out, int t, unsigned gmask,
-                               float *stage, int32_t *info_bi) {
+    __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
+                               const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo) {
         if (w == W) {
-            if constexpr (W <= 8)
-                f32_border<W, 8>(bd, sband, out, t, gmask, stage, info_bi);
-            else
-                f32_border<W, 16>(bd, sband, out, t, gmask, stage, info_bi);
+            f32_border<W>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
             return;
         }
-        F32BorderDispatch<W - 1>::run(w, bd, sband, out, t, gmask, stage, info_bi);
+        F32BorderDispatch<W - 1>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
     }
 };
 template <>
 struct F32BorderDispatch<0> {
-    __device__ static void run(int, const BlockDesc &, const float *, double *, int, unsigned, float *,
-                               int32_t *) {}
+    __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
+                               const int *, const int *, float *, int *) {}
 };
 
-// One CTA per F32Cta slice: 16 groups of 8 lanes (W <= 8) or 8 groups of 16.
-__global__ void __launch_bounds__(128) k_f32_border_pass(const F32Cta *__restrict__ ctas,
-                                                         const int32_t *__restrict__ items,
-                                                         const BlockDesc *__restrict__ blocks,
-                                                         const float *__restrict__ sh, double *__restrict__ out,
-                                                         int32_t *__restrict__ info) {
-    __shared__ float stg[16 * 2 * kChunk * 9];  // = 8 x 2 x kChunk x 17 + 32 floats
-    const F32Cta c = ctas[blockIdx.x];
-    const int G2 = c.w <= 8 ? 8 : 16;
-    const int lane = threadIdx.x & 31;
-    const int t = lane % G2, grp = threadIdx.x / G2;
-    const unsigned gmask = (G2 == 8 ? 0xFFu : 0xFFFFu) << (lane - t);
-    if (grp >= c.count) return;
-    const int bi = items[c.first + grp];
-    if (info[bi] != 0) return;
-    const BlockDesc bd = blocks[bi];
-    F32BorderDispatch<16>::run(bd.w, bd, sh + bd.off_pband, out, t, gmask, stg + grp * 2 * kChunk * (c.w + 1),
-                               info + bi);
+// floats: three staged periods, two periods of L21 values and the last W
+// columns of A21, W = 16
+constexpr int kF32BorderStage = 3 * 17 * 17 * 32 + 2 * 16 * 17 * 32 + 16 * 16 * 32;
+
+// Per-slice block table in shared memory: offsets, sizes, and whether the
+// block is still factored in FP32 (its band pass passed the pivot floor).
+struct SliceBlocks {
+    int64_t off[32];
+    int n[32], live[32], bi[32];
+};
+
+__device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice &sl, const int32_t *items,
+                                                  const BlockDesc *blocks, const int32_t *info) {
+    if (threadIdx.x < 32) {
+        const int L = threadIdx.x;
+        int64_t off = 0;
+        int n = 2 * sl.w + 2, live = 0, bi = 0;
+        if (L < sl.count) {
+            bi = items[sl.first + L];
+            const BlockDesc bd = blocks[bi];
+            off = bd.off_pband;
+            n = bd.n;
+            live = info[bi] == 0;
+        }
+        t.off[L] = off;
+        t.n[L] = n;
+        t.live[L] = live;
+        t.bi[L] = bi;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBorderThreads) k_f32_border_pass(const F32Slice *__restrict__ slices,
+                                                                    const int32_t *__restrict__ items,
+                                                                    const BlockDesc *__restrict__ blocks,
+                                                                    const float *__restrict__ sh,
+                                                                    float *__restrict__ l21,
+                                                                    const double *__restrict__ out,
+                                                                    int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ SliceBlocks t;
+    __shared__ int binfo[32];
+    const F32Slice sl = slices[blockIdx.x];
+    load_slice_blocks(t, sl, items, blocks, info);
+    F32BorderDispatch<16>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm, binfo);
+    if (threadIdx.x < 32 && t.live[threadIdx.x] && sl.w > 0) info[t.bi[threadIdx.x]] = binfo[threadIdx.x];
+}
+
+// The factor back to the FP64 blocks: L11 rows from the band shadow and
+// L21 rows from the border buffer, 64 elements x 32 blocks per CTA, through
+// a shared-memory transpose (coalesced on both sides).  Blocks sent to the
+// FP64 rescue are skipped.
+__global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles, const F32Slice *__restrict__ slices,
+                                                 const int32_t *__restrict__ items,
+                                                 const BlockDesc *__restrict__ blocks,
+                                                 const int32_t *__restrict__ info, const float *__restrict__ sh,
+                                                 const float *__restrict__ l21, double *__restrict__ out) {
+    __shared__ float tile[64][33];
+    __shared__ int64_t s_off[32];
+    __shared__ int s_n[32], s_live[32];
+    const int2 tl = tiles[blockIdx.x];
+    const F32Slice sl = slices[tl.x];
+    const int W = sl.w, RL = W + 1;
+    const bool part21 = tl.y < 0;
+    const int e0 = part21 ? -1 - tl.y : tl.y;
+    if (threadIdx.x < 32) {
+        const int L = threadIdx.x;
+        int64_t off = 0;
+        int n = 0, live = 0;
+        if (L < sl.count) {
+            const int bi = items[sl.first + L];
+            const BlockDesc bd = blocks[bi];
+            off = bd.off_pband;
+            n = bd.n;
+            live = info[bi] != kRescue;
+        }
+        s_off[L] = off;
+        s_n[L] = n;
+        s_live[L] = live;
+    }
+    const int kc = sl.rows - W;
+    const int lim = part21 ? W * kc : sl.rows * RL;
+    const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
+    for (int i = threadIdx.x; i < 64 * 32; i += 256) {
+        const int e = i >> 5, L = i & 31;
+        tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 32; i += 256) {
+        const int L = i >> 6, e = i & 63, ee = e0 + e;
+        if (!s_live[L] || ee >= lim) continue;
+        const int n = s_n[L], m = n - W;
+        int64_t dst;
+        if (!part21) {
+            const int row = ee / RL, d = ee - row * RL;
+            if (row >= m || d > row) continue;
+            dst = s_off[L] + ee;
+        } else {
+            const int bb = ee / kc, k = ee - bb * kc;
+            if (k >= m) continue;
+            dst = s_off[L] + (int64_t)n * RL + (int64_t)bb * n + k;
+        }
+        out[dst] = f32_to_f64_bits(tile[e][L]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1300,19 +1487,23 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
     if (precision == SYMPIX_PREC_FP64)
         launch_band<ArF64>(pl, dense, blocks, info, st);
     else if (precision == SYMPIX_PREC_FP32 && !dense) {
-        const int nf = (int)pl->f32_items.size();
-        if (nf) {
-            k_f32_shadow_in<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow.p);
+        const int ns = (int)pl->f32_slices.size();
+        if (ns) {
+            const F32Slice *sl = pl->d_f32_slices.p;
+            k_f32_shadow_in<<<(unsigned)pl->f32_tiles.size(), 256, 0, st>>>(
+                pl->d_f32_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow_il.p);
             const size_t smem = (size_t)kF32BandStage * sizeof(float);
             cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_f32_band_pass<<<(unsigned)pl->f32_band_ctas.size(), 32, smem, st>>>(
-                (const F32Cta *)pl->d_f32_band_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p, info,
-                (float)pl->fp32_pivot_floor);
-            k_f32_shadow_out<<<nf, 256, 0, st>>>(pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow.p, blocks);
-            if (!pl->f32_border_ctas.empty())
-                k_f32_border_pass<<<(unsigned)pl->f32_border_ctas.size(), 128, 0, st>>>(
-                    (const F32Cta *)pl->d_f32_border_ctas.p, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow.p,
-                    blocks, info);
+            k_f32_band_pass<<<(unsigned)ns, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
+                                                           pl->d_shadow_il.p, info, (float)pl->fp32_pivot_floor);
+            const size_t bs = (size_t)kF32BorderStage * sizeof(float);
+            cudaFuncSetAttribute(k_f32_border_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
+            k_f32_border_pass<<<(unsigned)ns, kBorderThreads, bs, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
+                                                                       pl->d_shadow_il.p, pl->d_l21_il.p, blocks,
+                                                                       info);
+            k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(
+                pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
+                pl->d_l21_il.p, blocks);
             // near-degenerate blocks: FP64 from the untouched FP64 input
             launch_band<ArF64>(pl, false, blocks, info, st, 1);
         }

@@ -111,6 +111,15 @@ struct SampleItem {
     int32_t q0;
 };
 
+// Up to 32 periodic-band blocks of one width w <= 16 factored together in
+// FP32: blocks f32_items[first .. first+count), at most `rows` rows each.
+// Their lane-interleaved band shadow starts at float offset `sh` (rows x
+// (w+1) x 32) and their FP32 border rows L21 at `l21` (w x (rows-w) x 32).
+struct F32Slice {
+    int32_t w, first, count, rows;
+    int64_t sh, l21;
+};
+
 struct sympix_plan_s {
     sympix_grid_t grid = nullptr;
     int nops = 0, ring0 = 0, ring1 = 0;
@@ -133,9 +142,14 @@ struct sympix_plan_s {
     // [3] dense format with n <= 1024; [4] everything else
     std::vector<int32_t> factor_items[6];
     // FP32 factorisation on a band shadow: periodic-band blocks with w <= 16
-    // grouped by exact width, and CTA slices of the band and border passes
+    // grouped by exact width into slices of up to 32 blocks; each slice's
+    // shadow is lane-interleaved (element e of its block L at 32 e + L)
     std::vector<int32_t> f32_items;
-    std::vector<int4> f32_band_ctas, f32_border_ctas;  // (w, first, count, 0)
+    std::vector<F32Slice> f32_slices;
+    std::vector<int2> f32_tiles;  // (slice, first element) of the band shadow transposes
+    std::vector<int2> f32_out_tiles;  // the same, then (slice, -1 - first element) of L21
+    int f32_slices_narrow = 0;    // slices with w <= 8 (they come first)
+    int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;
     sympix::DevBuf<double> d_slot_u;         // u = 1 - cos(gamma) per slot
@@ -152,8 +166,12 @@ struct sympix_plan_s {
     sympix::DevBuf<SampleItem> d_items_dense;
     sympix::DevBuf<int32_t> d_factor_items[6];
     sympix::DevBuf<int32_t> d_f32_items;
-    sympix::DevBuf<int4> d_f32_band_ctas, d_f32_border_ctas;
-    sympix::DevBuf<float> d_shadow;  // FP32 copy of the band rows
+    sympix::DevBuf<F32Slice> d_f32_slices;
+    sympix::DevBuf<int2> d_f32_tiles;
+    sympix::DevBuf<float> d_shadow_il;  // lane-interleaved FP32 band rows, w <= 16
+    sympix::DevBuf<float> d_l21_il;     // lane-interleaved FP32 border rows, w <= 16
+    sympix::DevBuf<int2> d_f32_out_tiles;
+    sympix::DevBuf<float> d_shadow;     // FP32 band rows of wide blocks, at their pband offsets
     bool table_ready = false;
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
 };

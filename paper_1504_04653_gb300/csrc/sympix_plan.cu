@@ -340,25 +340,51 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         pl->factor_items[list].push_back(b);
     }
 
-    // FP32 factorisation on a band shadow: blocks by exact width, CTA slices
+    // FP32 factorisation on a band shadow: blocks by exact width (most
+    // expensive first, so a slice holds blocks of similar length), slices of
+    // up to 32, each with its lane-interleaved shadow region
     {
         std::vector<int32_t> byw[17];
         for (int b : order) {
             const BlockDesc &bd = pl->blocks[b];
             if (bd.format == SYMPIX_BLOCK_PBAND && bd.w <= 16) byw[bd.w].push_back(b);
         }
+        int64_t sh = 0, l21 = 0;
+        std::vector<int2> tiles21;
         for (int w = 0; w <= 16; ++w) {
             const int first = (int)pl->f32_items.size(), cnt = (int)byw[w].size();
             pl->f32_items.insert(pl->f32_items.end(), byw[w].begin(), byw[w].end());
-            const int pb = w <= 8 ? 32 : 16, pr = w <= 8 ? 16 : 8;
-            for (int i = 0; i < cnt; i += pb) pl->f32_band_ctas.push_back(make_int4(w, first + i, std::min(pb, cnt - i), 0));
-            for (int i = 0; i < cnt; i += pr)
-                pl->f32_border_ctas.push_back(make_int4(w, first + i, std::min(pr, cnt - i), 0));
+            for (int i = 0; i < cnt; i += 32) {
+                F32Slice sl;
+                sl.w = w;
+                sl.first = first + i;
+                sl.count = std::min(32, cnt - i);
+                sl.rows = 0;
+                for (int j = 0; j < sl.count; ++j) sl.rows = std::max(sl.rows, pl->blocks[byw[w][i + j]].n);
+                sl.sh = sh;
+                sl.l21 = l21;
+                const int64_t elems = (int64_t)sl.rows * (w + 1), elems21 = (int64_t)w * (sl.rows - w);
+                for (int64_t e0 = 0; e0 < elems; e0 += 64)
+                    pl->f32_tiles.push_back(make_int2((int)pl->f32_slices.size(), (int)e0));
+                for (int64_t e0 = 0; e0 < elems21; e0 += 64)
+                    tiles21.push_back(make_int2((int)pl->f32_slices.size(), (int)(-1 - e0)));
+                sh += 32 * elems;
+                l21 += 32 * elems21;
+                if (w <= 8) ++pl->f32_slices_narrow;
+                pl->f32_slices.push_back(sl);
+            }
         }
+        pl->size_shadow_il = sh;
+        pl->size_l21_il = l21;
+        pl->f32_out_tiles = pl->f32_tiles;
+        pl->f32_out_tiles.insert(pl->f32_out_tiles.end(), tiles21.begin(), tiles21.end());
     }
-    if ((rc = pl->d_f32_items.upload(pl->f32_items)) || (rc = pl->d_f32_band_ctas.upload(pl->f32_band_ctas)) ||
-        (rc = pl->d_f32_border_ctas.upload(pl->f32_border_ctas)) ||
-        (rc = pl->d_shadow.alloc(std::max<int64_t>(pl->size_pband, 1))))
+    if ((rc = pl->d_f32_items.upload(pl->f32_items)) || (rc = pl->d_f32_slices.upload(pl->f32_slices)) ||
+        (rc = pl->d_f32_tiles.upload(pl->f32_tiles)) ||
+        (rc = pl->d_f32_out_tiles.upload(pl->f32_out_tiles)) ||
+        (rc = pl->d_shadow_il.alloc(std::max<int64_t>(pl->size_shadow_il, 1))) ||
+        (rc = pl->d_l21_il.alloc(std::max<int64_t>(pl->size_l21_il, 1))) ||
+        (rc = pl->d_shadow.alloc(pl->factor_items[5].empty() ? 1 : std::max<int64_t>(pl->size_pband, 1))))
         return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
         (rc = pl->d_items_dense.upload(pl->items_dense)))
@@ -424,9 +450,10 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
                l2 = !pl->factor_items[2].empty();
     if (factor_precision == SYMPIX_PREC_FP32 && pband) {
         if (!pl->f32_items.empty()) {
-            // shadow in, band pass, shadow out, border pass, then the FP64
-            // rescue launches (which return at once for blocks that need none)
-            f = 3 + (pl->f32_border_ctas.empty() ? 0 : 1);
+            // shadow in, band pass, border pass (with the corners), FP64
+            // write-back, then the FP64 rescue launches (which return at
+            // once for blocks that need none)
+            f = 4;
             f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
