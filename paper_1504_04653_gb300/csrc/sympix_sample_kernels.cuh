@@ -69,13 +69,23 @@ __device__ __forceinline__ void same_count_entry(typename A::V (&acc)[WMAX + 1],
 #pragma unroll
     for (int k = 0; k < K; ++k) t[k] = A::tab(tb, tb32, tblo, tab + k);
     V wv[2 * K - 1];
+    const int p0 = q - (K - 1);
+    if (nstride == 1 && p0 >= 0 && p0 + 2 * K - 2 < n) {
+        // the window does not wrap: one base pointer, immediate offsets
 #pragma unroll
-    for (int i = 0; i < 2 * K - 1; ++i) {
-        const int s = i - (K - 1);
-        int p = q + s;
-        p += p < 0 ? n : 0;
-        p -= p >= n ? n : 0;
-        wv[i] = A::mul(t[s < 0 ? -s : s], A::nval(n64, n32, nlo, (int64_t)p * nstride));
+        for (int i = 0; i < 2 * K - 1; ++i) {
+            const int s = i - (K - 1);
+            wv[i] = A::mul(t[s < 0 ? -s : s], A::nval(n64 + p0, n32 + p0, nlo + p0, i));
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2 * K - 1; ++i) {
+            const int s = i - (K - 1);
+            int p = q + s;
+            p += p < 0 ? n : 0;
+            p -= p >= n ? n : 0;
+            wv[i] = A::mul(t[s < 0 ? -s : s], A::nval(n64, n32, nlo, (int64_t)p * nstride));
+        }
     }
 #pragma unroll
     for (int d = 0; d <= 2 * K - 2; ++d) {

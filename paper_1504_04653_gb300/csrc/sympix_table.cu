@@ -2,13 +2,14 @@
 // addition-theorem) and d(x) likewise, at every symmetry-class slot, in FP64.
 //
 // x is carried as u = 1 - x (exact haversine form from the plan).  P_l is
-// advanced on its differences D_l = P_l - P_{l-1}:
-//   D_{l+1} = A_l D_l - B_l u P_l,  P_{l+1} = P_l + D_{l+1},
-//   A_l = l / (l+1),  B_l = (2l+1) / (l+1),
-// the three-term recurrence rearranged for x near 1, where the kernel is
-// steep (d b / d x ~ b / sigma^2) and rounding x itself would cost ~1e-10.
-// Coefficients (A_l, B_l) and the scaled c'_l = (2l+1) c_l / (4 pi) are
-// staged once per launch in global memory and read as warp-uniform loads.
+// advanced on its scaled differences E_l = l (P_l - P_{l-1}):
+//   E_{l+1} = E_l - (2l+1) u P_l,  P_{l+1} = P_l + E_{l+1} / (l+1),
+// which is the three-term recurrence (l+1) P_{l+1} = (2l+1) x P_l - l P_{l-1}
+// rearranged for x near 1, where the kernel is steep (d b / d x ~ b / sigma^2)
+// and rounding x itself would cost ~1e-10.  One step is a product and three
+// fused multiply-adds on the FP64 pipe, the slowest pipe this kernel uses.
+// The coefficients (-(2l+1), 1/(l+1)) and the scaled c'_l = (2l+1) c_l / (4 pi)
+// are staged once per launch in global memory and read as warp-uniform loads.
 #include "sympix_internal.cuh"
 
 namespace sympix {
@@ -19,8 +20,8 @@ __global__ void k_table_coeffs(int lmax, int nops, const double *__restrict__ bl
     const int L1 = lmax + 1;
     if (i < L1) {
         double l = (double)i;
-        rec[2 * i] = l / (l + 1.0);
-        rec[2 * i + 1] = (2.0 * l + 1.0) / (l + 1.0);
+        rec[2 * i] = -(2.0 * l + 1.0);
+        rec[2 * i + 1] = 1.0 / (l + 1.0);
     }
     if (i < nops * L1) {
         const double f = (2.0 * (double)(i % L1) + 1.0) / (4.0 * kPi);
@@ -68,10 +69,9 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
                 if (same) sd[o] = fma(cd[(op0 + o) * L1 + 1], p, sd[o]);
             }
     }
-    for (int l = 1; l < lmax; ++l) {
-        const double A = rec[2 * l], B = rec[2 * l + 1];
-        dlt = fma(A, dlt, -B * (u * p));
-        p += dlt;
+    for (int l = 1; l < lmax; ++l) {  // dlt = E_l on entry (E_1 = -u)
+        dlt = fma(rec[2 * l], u * p, dlt);
+        p = fma(dlt, rec[2 * l + 1], p);
 #pragma unroll
         for (int o = 0; o < NOPS; ++o)
             if (o < nops) {
