@@ -829,14 +829,13 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict
 // through shared memory to the corner sums S = L21 L21^T, which the 8 warps
 // share pair by pair.  At the end one thread per block factors its corner
 // A22 - S = L22 L22^T in FP64.
-constexpr int kBorderThreads = 256;
-
-template <int W>
+template <int W, int NT>
 __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
                                            const double *__restrict__ out, const int64_t *s_off, const int *s_n,
                                            const int *s_live, float *stage, int *binfo) {
     constexpr int RL = W + 1, CH = RL * RL;
-    constexpr int R = (W + 7) / 8;  // border rows per lane
+    constexpr int NWARP = NT / 32;
+    constexpr int R = (W + NWARP - 1) / NWARP;  // border rows per lane
     const int lane = threadIdx.x & 31, b0 = (threadIdx.x >> 5) * R;
     const bool rows = b0 < W;       // warp-uniform: this warp owns border rows
     const int n = s_n[lane], m = n - W;
@@ -849,14 +848,14 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
             float *dst = stage + (per % 3) * CH * 32;
             const float *src = shs + (int64_t)r0 * RL * 32;
-            for (int i = threadIdx.x; i < CH * 8; i += kBorderThreads) cp_async16(dst + 4 * i, src + 4 * i);
+            for (int i = threadIdx.x; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
         }
         cp_async_commit();
     };
     float *vbuf = stage + 3 * CH * 32;  // two periods of L21 values, [b][column][lane]
     float *vb = vbuf;                   // the current period's
     float *abuf = vbuf + 2 * W * RL * 32;  // A21 at the last W columns, [b][c][lane]: A[m+b][m-W+c]
-    for (int i = threadIdx.x; i < W * W * 32; i += kBorderThreads) {
+    for (int i = threadIdx.x; i < W * W * 32; i += NT) {
         const int L = i & 31, bc = i >> 5, bb = bc / (W > 0 ? W : 1), c = bc - bb * W;
         float v = 0.0f;
         if (s_live[L]) {
@@ -912,15 +911,15 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         }
     };
     // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b: the
-    // W (W+1)/2 pairs are dealt round-robin to the 8 warps, lane = block;
+    // W (W+1)/2 pairs are dealt round-robin to the warps, lane = block;
     // each period's L21 values pass through vbuf
-    constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + 7) / 8;
+    constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + NWARP - 1) / NWARP;
     const int wq = threadIdx.x >> 5;
     int pb[NP > 0 ? NP : 1], pb2[NP > 0 ? NP : 1];
     float sacc[NP > 0 ? NP : 1];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        int j = wq + 8 * i, bb = 0;
+        int j = wq + NWARP * i, bb = 0;
         while (j > bb) {  // pair j = bb (bb+1)/2 + b2
             j -= bb + 1;
             ++bb;
@@ -932,7 +931,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     auto accumulate = [&](const float *v) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            if (wq + 8 * i >= NPAIR) break;
+            if (wq + NWARP * i >= NPAIR) break;
             const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
 #pragma unroll
             for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
@@ -968,7 +967,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NP; ++i)
-        if (wq + 8 * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+        if (wq + NWARP * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
     __syncthreads();
     if (threadIdx.x < 32 && live) {
         double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
@@ -998,19 +997,19 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     }
 }
 
-template <int W>
+template <int W, int WMIN, int NT>
 struct F32BorderDispatch {
     __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
                                const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo) {
         if (w == W) {
-            f32_border<W>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
+            f32_border<W, NT>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
             return;
         }
-        F32BorderDispatch<W - 1>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
+        F32BorderDispatch<W - 1, WMIN, NT>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
     }
 };
-template <>
-struct F32BorderDispatch<0> {
+template <int WMIN, int NT>
+struct F32BorderDispatch<WMIN - 1, WMIN, NT> {
     __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
                                const int *, const int *, float *, int *) {}
 };
@@ -1047,6 +1046,9 @@ __device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice
     __syncthreads();
 }
 
+// One CTA of kBorderThreads per slice: one border row per warp.
+constexpr int kBorderThreads = 512;
+
 __global__ void __launch_bounds__(kBorderThreads) k_f32_border_pass(const F32Slice *__restrict__ slices,
                                                                     const int32_t *__restrict__ items,
                                                                     const BlockDesc *__restrict__ blocks,
@@ -1059,7 +1061,8 @@ __global__ void __launch_bounds__(kBorderThreads) k_f32_border_pass(const F32Sli
     __shared__ int binfo[32];
     const F32Slice sl = slices[blockIdx.x];
     load_slice_blocks(t, sl, items, blocks, info);
-    F32BorderDispatch<16>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm, binfo);
+    F32BorderDispatch<16, 1, kBorderThreads>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm,
+                                                  binfo);
     if (threadIdx.x < 32 && t.live[threadIdx.x] && sl.w > 0) info[t.bi[threadIdx.x]] = binfo[threadIdx.x];
 }
 
@@ -1103,21 +1106,20 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
         tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 32; i += 256) {
-        const int L = i >> 6, e = i & 63, ee = e0 + e;
-        if (!s_live[L] || ee >= lim) continue;
+    // every element of this thread has the same e (its lanes differ): the
+    // element's (row, offset) or (border row, column) is formed once
+    const int e = threadIdx.x & 63, ee = e0 + e;
+    if (ee >= lim) return;
+    const int q = part21 ? ee / kc : ee / RL;          // border row b, or band row
+    const int r = part21 ? ee - q * kc : ee - q * RL;  // column k, or offset d
+#pragma unroll
+    for (int L = threadIdx.x >> 6; L < 32; L += 4) {
         const int n = s_n[L], m = n - W;
-        int64_t dst;
-        if (!part21) {
-            const int row = ee / RL, d = ee - row * RL;
-            if (row >= m || d > row) continue;
-            dst = s_off[L] + ee;
-        } else {
-            const int bb = ee / kc, k = ee - bb * kc;
-            if (k >= m) continue;
-            dst = s_off[L] + (int64_t)n * RL + (int64_t)bb * n + k;
+        const bool ok = s_live[L] && (part21 ? r < m : (q < m && r <= q));
+        if (ok) {
+            const int64_t dst = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q * n + r : s_off[L] + ee;
+            out[dst] = f32_to_f64_bits(tile[e][L]);
         }
-        out[dst] = f32_to_f64_bits(tile[e][L]);
     }
 }
 

@@ -370,7 +370,6 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                     tiles21.push_back(make_int2((int)pl->f32_slices.size(), (int)(-1 - e0)));
                 sh += 32 * elems;
                 l21 += 32 * elems21;
-                if (w <= 8) ++pl->f32_slices_narrow;
                 pl->f32_slices.push_back(sl);
             }
         }
