@@ -141,6 +141,9 @@ class Clocks:
 
 # -- the GPU arm ---------------------------------------------------------------------------
 
+S_BLOCK_PBAND = 0  # the C header's SYMPIX_BLOCK_PBAND
+
+
 def factor_flops(plan):
     tot = 0.0
     for o in range(plan.nops):
@@ -152,6 +155,63 @@ def factor_flops(plan):
             else:
                 tot += n ** 3 / 3.0
     return tot
+
+
+ALU_PEAK = {"fp64": (FP64_NOMINAL, "nominal FP64 1.25 TFLOP/s (a DFMA probe measured 1.197)"),
+            "fp32": (FP32_NOMINAL, "nominal FP32 80.5 TFLOP/s (an FFMA probe measured 73.1)"),
+            "fp32x2": (FP32_NOMINAL, "nominal FP32 80.5 TFLOP/s; a split product costs ~16 FP32 flops")}
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel from one ncu capture of (workload, precision), as summarised under
+# profiles/; an entry is removed when its kernel changes.
+TRAFFIC = {}
+
+
+def kernel_work(plan, grid, wl, elements, sprec, fprec):
+    """Algorithmic work of one launch of each kernel: (bound, amount, type),
+    amount in bytes for "hbm" and flops for "alu" (type = the arithmetic)."""
+    geo = [plan.block_layout("pband", o, j) for o in range(plan.nops) for j in range(plan.ring0, plan.ring1)]
+    f32 = [(n, w) for _, n, w, fmt in geo if fmt == S_BLOCK_PBAND and w <= 16]
+    band = sum(n * (w + 1) for n, w in f32)
+    l11 = sum((n - w) * (w + 1) for n, w in f32)
+    l21 = sum(w * (n - w) for n, w in f32)
+    npix = grid.npix * plan.nops
+    sample_flops = 2.0 * plan.ntriples + plan.nmults
+    sample_bytes = elements * 8 + npix * (8 if sprec == "fp64" else 16)
+    t_hbm = sample_bytes / (peaks().get("hbm_gbs", 6800.0) * 1e9)
+    t_alu = sample_flops / ALU_PEAK[sprec][0]
+    return {
+        "k_table": ("alu", plan.nslots * plan.nops * (wl.lmax - 1) * 7.0, "fp64"),
+        "k_table_coeffs": ("hbm", (wl.lmax + 1) * plan.nops * 32.0, "fp64"),
+        "k_split_ninv": ("hbm", npix * 16.0, sprec),
+        "k_sample_pband": ("hbm", sample_bytes, sprec) if t_hbm >= t_alu else ("alu", sample_flops, sprec),
+        "k_f32_shadow_in": ("hbm", band * 12.0, "fp32"),
+        "k_f32_band_pass": ("alu", float(sum((n - w) * (w * (w + 1) + w + 2) for n, w in f32)), "fp32"),
+        "k_f32_border_pass": ("alu", float(sum((n - w) * (2 * w * w + w + w * (w + 1)) for n, w in f32)), "fp32"),
+        "k_f32_out": ("hbm", (l11 + l21) * 12.0, "fp32"),
+        "k_factor_band": ("alu", factor_flops(plan), fprec),
+    }
+
+
+def rank_workload(wl, rank):
+    """Rank r's independent problem: the workload with every seed shifted by r."""
+    from paper_1504_04653_gb300 import workloads as W
+    return W.Workload(wl.name, wl.lmax, wl.fwhm_arcmin, wl.band_deg, [s + rank for s in wl.seeds], wl.desc)
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(elements_per_rank, ms_max, world):
+    """Whole-job throughput: every rank's elements over the slowest rank's time."""
+    return world * elements_per_rank / (ms_max * 1e-3)
 
 
 def main():
@@ -179,7 +239,7 @@ def main():
     from paper_1504_04653_gb300 import workloads as W
 
     wl = W.WORKLOADS[args.workload]
-    wl = W.Workload(wl.name, wl.lmax, wl.fwhm_arcmin, wl.band_deg, [s + rank for s in wl.seeds], wl.desc)
+    wl = rank_workload(wl, rank)
     grid = S.Grid(wl.lmax)
     plan = S.Plan(grid, wl.radii())
     nbytes, elements = plan.blocks_size("pband")
@@ -253,12 +313,8 @@ def main():
     info_h = info.cpu().numpy()
     sampled_main = None
     ms_step = float(main_st.sum(axis=1).mean())
-    ms_max = ms_step
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * elements / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms_step, world, dev)
+    value = job_value(elements, ms_max, world)
 
     # other contraction arms (same steps) and their accuracy against FP64
     arms = {}
@@ -349,53 +405,52 @@ def main():
         e2e = {"value": world * elements / (ms * 1e-3), "unit": "elements/s", "ms_per_step": ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant stage, against the peak of the arithmetic it runs in
+    # per-kernel device times: a traced pass of the same steps (direct calls,
+    # an event after every launch), then the roofline of the dominant kernel
+    # against the peak of the arithmetic (or memory) that bounds it
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0) * 1e9
     stages = dict(zip(["table", "sample", "factor"], main_st.mean(axis=0).tolist()))
-    dominant = max(stages, key=stages.get)
     sprec, fprec = args.precision.split(":")
-    alu_peak = {"fp64": (FP64_NOMINAL, "nominal FP64 1.25 TFLOP/s (a DFMA probe measured 1.197)"),
-                "fp32": (FP32_NOMINAL, "nominal FP32 80.5 TFLOP/s (an FFMA probe measured 73.1)"),
-                "fp32x2": (FP32_NOMINAL, "nominal FP32 80.5 TFLOP/s; split products cost ~16 FP32 flops each")}
-    L = wl.lmax
-    table_flops = plan.nslots * plan.nops * (L - 1) * 7.0
-    sample_flops = 2.0 * plan.ntriples + plan.nmults
-    sample_bytes = elements * 8 + grid.npix * plan.nops * (8 if sprec == "fp64" else 16)
-    if dominant == "table":
-        peak, src = alu_peak["fp64"]
-        roof = {"kernel": "k_table", "bound": "alu", "achieved": table_flops / (stages["table"] * 1e-3) / 1e12,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "peak_source": src}
-    elif dominant == "factor":
-        ff = factor_flops(plan)
-        peak, src = alu_peak[fprec]
-        roof = {"kernel": "k_f32_band_pass + k_f32_border_pass" if fprec == "fp32" else "k_factor_*",
-                "bound": "alu", "achieved": ff / (stages["factor"] * 1e-3) / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "peak_source": src,
-                "note": "per-block elimination is a chain of n dependent steps; latency, not ALU rate, bounds it"}
+    per_kernel = {}
+    plan.set_trace(True)
+    sp, fp = args.precision.split(":")
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            plan.trace_read()  # drop anything recorded before this step
+            S.sympix_kernel_table(plan, bl, dl, stream=stream)
+            S.sympix_sample_blocks(plan, ninv, precision=sp, storage="pband", out=blocks, stream=stream)
+            S.sympix_factor_blocks(plan, blocks, storage="pband", precision=fp, info=info, stream=stream)
+        for name, ms in plan.trace_read():
+            per_kernel.setdefault(name, []).append(ms)
+    plan.set_trace(False)
+    kern_ms = {k: float(np.mean(v)) for k, v in per_kernel.items()}
+    dominant = max(kern_ms, key=kern_ms.get)
+    work = kernel_work(plan, grid, wl, elements, sprec, fprec)
+    bound, amount, ktype = work.get(dominant, ("alu", 0.0, fprec))
+    if bound == "hbm":
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": amount / (kern_ms[dominant] * 1e-3) / 1e9,
+                "peak": hbm / 1e9, "unit": "GB/s", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": amount}
     else:
-        t_hbm = sample_bytes / hbm
-        peak, src = alu_peak[sprec]
-        t_alu = sample_flops / peak
-        if t_hbm >= t_alu:
-            roof = {"kernel": "k_sample_pband", "bound": "hbm",
-                    "achieved": sample_bytes / (stages["sample"] * 1e-3) / 1e9, "peak": hbm / 1e9,
-                    "unit": "GB/s", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-        else:
-            roof = {"kernel": "k_sample_pband", "bound": "alu",
-                    "achieved": sample_flops / (stages["sample"] * 1e-3) / 1e12, "peak": peak / 1e12,
-                    "unit": "TFLOP/s", "peak_source": src}
+        peak, src = ALU_PEAK[ktype]
+        roof = {"kernel": dominant, "bound": "alu", "achieved": amount / (kern_ms[dominant] * 1e-3) / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "peak_source": src, "algorithmic_flops_per_launch": amount}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["stage_ms"] = stages[dominant]
-    # the other stages against their own bounds, for context
-    others = {
-        "table": {"achieved_tflops": table_flops / (stages["table"] * 1e-3) / 1e12,
-                  "frac_of_fp64_nominal": table_flops / (stages["table"] * 1e-3) / FP64_NOMINAL},
-        "sample": {"achieved_gbs": sample_bytes / (stages["sample"] * 1e-3) / 1e9,
-                   "frac_of_hbm": sample_bytes / (stages["sample"] * 1e-3) / hbm,
-                   "achieved_tflops": sample_flops / (stages["sample"] * 1e-3) / 1e12},
-    }
+    roof["traffic"] = TRAFFIC.get((wl.name, args.precision, dominant))
+    roof["kernel_ms"] = kern_ms[dominant]
+    roof["timing"] = "CUDA events around each launch on the launching stream, traced pass of the same steps"
+    # every kernel against its own bound, for context
+    kernels = {}
+    for name, ms in kern_ms.items():
+        b, a, t = work.get(name, ("alu", 0.0, fprec))
+        if b == "hbm":
+            kernels[name] = {"ms": round(ms, 4), "bound": "hbm", "gbs": a / (ms * 1e-3) / 1e9,
+                             "frac": a / (ms * 1e-3) / hbm}
+        else:
+            kernels[name] = {"ms": round(ms, 4), "bound": "alu", "tflops": a / (ms * 1e-3) / 1e12,
+                             "frac": a / (ms * 1e-3) / ALU_PEAK[t][0]}
 
     if args.launch == "graph":
         launches = graph_step(args.precision).kernels(S.STAGE_ALL)
@@ -416,7 +471,7 @@ def main():
                    "launch": "one CUDA graph replay per stage" if args.launch == "graph" else "direct calls",
                    "parallelism": f"independent problem per GPU x{world}"},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
-        "stage_rooflines": others,
+        "kernel_rooflines": kernels,
         "arms": arms, "accuracy": acc, "roofline": roof, "e2e": e2e,
         "gpu_launches": launches * args.steps, "clocks": clk,
         "blocks": int(plan.nblocks),

@@ -138,9 +138,20 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
 #define SYMPIX_OPT_FP32_PIVOT_FLOOR 1 /* FP32 factor: a block is refactored in FP64 when a pivot
                                           falls below floor x its row's original diagonal
                                           (default 0.05; 0 never, > 1 always) */
+#define SYMPIX_OPT_TRACE 2            /* 1: record a CUDA event after every kernel launch of
+                                          sympix_kernel_table / _sample_blocks / _factor_blocks
+                                          (direct calls, not stream capture); 0: off (default) */
 
 /* Set a plan option; takes effect for the following calls on the plan. */
 int sympix_plan_option(sympix_plan_t plan, int option, double value);
+
+/* Per-kernel device times of the traced calls since the last read
+ * (SYMPIX_OPT_TRACE): waits for the last recorded event, then writes up to
+ * `cap` spans, each the kernel (or group of launches) `names[i]` (static
+ * strings) and its duration `ms[i]` in milliseconds, in launch order;
+ * *count receives the number of spans recorded (at most 256 per read).
+ * Clears the trace.  Not part of the method: a measurement aid. */
+int sympix_trace_read(sympix_plan_t plan, int cap, const char **names, float *ms, int *count);
 
 /* Counts of a plan (any pointer may be NULL): nslots symmetry-class slots
  * (kernel values per operator); npairs coupled ordered ring pairs summed over

@@ -620,13 +620,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-// One CTA per 64 elements x 32 blocks of a slice.
+// One CTA per kTileE elements x 32 blocks of a slice.
 __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ tiles,
                                                        const F32Slice *__restrict__ slices,
                                                        const int32_t *__restrict__ items,
                                                        const BlockDesc *__restrict__ blocks,
                                                        const double *__restrict__ out, float *__restrict__ sh) {
-    __shared__ float tile[64][33];
+    __shared__ float tile[kTileE][33];
     __shared__ int64_t s_off[32];
     __shared__ int s_cnt[32];
     const int2 tl = tiles[blockIdx.x];
@@ -644,8 +644,8 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
         s_cnt[threadIdx.x] = cnt;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
-        const int L = i >> 6, e = i & 63;
+    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
+        const int L = i / kTileE, e = i % kTileE;
         float v = 0.0f;
         if (e0 + e < s_cnt[L]) v = f64_to_f32_bits(out[s_off[L] + e0 + e]);
         tile[e][L] = v;
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
     __syncthreads();
     const int lim = sl.rows * RL;
     float *dst = sh + sl.sh + (int64_t)e0 * 32;
-    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
         const int e = i >> 5, L = i & 31;
         if (e0 + e < lim) dst[e * 32 + L] = tile[e][L];
     }
@@ -877,9 +877,12 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         for (int c = 0; c < RL; ++c) y[r][c] = 0.0f;
     }
     // column k = p RL + PH; src = this lane's staged rows of period p
-    auto column = [&](auto PHc, auto FIRSTc, const float *src, int kbase) {
+    // TAIL: some block of the warp reaches its last W columns (A21's band
+    // part) or its end in this period; otherwise no select is needed
+    auto column = [&](auto PHc, auto FIRSTc, auto TAILc, const float *src, int kbase) {
         constexpr int PH = decltype(PHc)::value;
         constexpr bool FIRST = decltype(FIRSTc)::value;  // p == 0: mask the columns left of 0
+        constexpr bool TAIL = decltype(TAILc)::value;
         const int k = kbase + PH;
         const float *row = src + PH * RL * 32;  // L11 row k: offset d at row[32 d]
         float lr[RL];
@@ -892,7 +895,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
             const int b = b0 + r;
             float acc = 0.0f;
             if constexpr (FIRST && PH < W) acc = aw[r][PH < W ? PH : 0];
-            {  // the last W columns, without a branch
+            if constexpr (TAIL) {  // the last W columns, without a branch
                 const int c = k - (m - W);
                 const float a = abuf[((b < W ? b : W - 1) * W + min(max(c, 0), W - 1)) * 32 + lane];
                 acc = (c >= 0 && c < W) ? a : acc;
@@ -902,11 +905,11 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
                 if (FIRST && PH - W + cc < 0) continue;  // left of column 0
                 acc = fmaf(-y[r][(PH - W + cc + RL) % RL], lr[W - cc], acc);
             }
-            const float val = (live && b < W && k < m) ? acc * rcp : 0.0f;
+            const float val = (!TAIL || (live && b < W && k < m)) ? acc * rcp : 0.0f;
             y[r][PH] = val;
             if (b < W) {
                 vb[(b * RL + PH) * 32 + lane] = val;
-                if (k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
+                if (!TAIL || k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
             }
         }
     };
@@ -949,11 +952,16 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         if (rows) {
             const float *src = stage + (p % 3) * CH * 32 + lane;
             const int kbase = p * RL;
+            // warp-uniform: does any block of the warp need the tail handling?
+            const bool tail = kbase + RL > kc - W || __any_sync(0xffffffffu, live && kbase + RL > m - W);
             if (p == 0) {
-                auto f = [&](auto PHc) { column(PHc, std::true_type{}, src, kbase); };
+                auto f = [&](auto PHc) { column(PHc, std::true_type{}, std::true_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            } else if (tail) {
+                auto f = [&](auto PHc) { column(PHc, std::false_type{}, std::true_type{}, src, kbase); };
                 StaticFor<0, RL>::run(f);
             } else {
-                auto f = [&](auto PHc) { column(PHc, std::false_type{}, src, kbase); };
+                auto f = [&](auto PHc) { column(PHc, std::false_type{}, std::false_type{}, src, kbase); };
                 StaticFor<0, RL>::run(f);
             }
         }
@@ -1075,7 +1083,7 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
                                                  const BlockDesc *__restrict__ blocks,
                                                  const int32_t *__restrict__ info, const float *__restrict__ sh,
                                                  const float *__restrict__ l21, double *__restrict__ out) {
-    __shared__ float tile[64][33];
+    __shared__ float tile[kTileE][33];
     __shared__ int64_t s_off[32];
     __shared__ int s_n[32], s_live[32];
     const int2 tl = tiles[blockIdx.x];
@@ -1101,19 +1109,19 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
     const int kc = sl.rows - W;
     const int lim = part21 ? W * kc : sl.rows * RL;
     const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
-    for (int i = threadIdx.x; i < 64 * 32; i += 256) {
+    for (int i = threadIdx.x; i < kTileE * 32; i += 256) {
         const int e = i >> 5, L = i & 31;
         tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
     }
     __syncthreads();
     // every element of this thread has the same e (its lanes differ): the
     // element's (row, offset) or (border row, column) is formed once
-    const int e = threadIdx.x & 63, ee = e0 + e;
+    const int e = threadIdx.x % kTileE, ee = e0 + e;
     if (ee >= lim) return;
     const int q = part21 ? ee / kc : ee / RL;          // border row b, or band row
     const int r = part21 ? ee - q * kc : ee - q * RL;  // column k, or offset d
 #pragma unroll
-    for (int L = threadIdx.x >> 6; L < 32; L += 4) {
+    for (int L = threadIdx.x / kTileE; L < 32; L += 256 / kTileE) {
         const int n = s_n[L], m = n - W;
         const bool ok = s_live[L] && (part21 ? r < m : (q < m && r <= q));
         if (ok) {
@@ -1486,33 +1494,44 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
         return set_error(SYMPIX_EINVAL, "sympix_factor_blocks: unknown precision %d", precision);
     cudaStream_t st = (cudaStream_t)stream;
     const bool dense = storage == SYMPIX_STORE_DENSE;
-    if (precision == SYMPIX_PREC_FP64)
+    trace_mark(pl, st, nullptr);
+    if (precision == SYMPIX_PREC_FP64) {
         launch_band<ArF64>(pl, dense, blocks, info, st);
+        trace_mark(pl, st, "k_factor_band");
+    }
     else if (precision == SYMPIX_PREC_FP32 && !dense) {
         const int ns = (int)pl->f32_slices.size();
         if (ns) {
             const F32Slice *sl = pl->d_f32_slices.p;
             k_f32_shadow_in<<<(unsigned)pl->f32_tiles.size(), 256, 0, st>>>(
                 pl->d_f32_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow_il.p);
+            trace_mark(pl, st, "k_f32_shadow_in");
             const size_t smem = (size_t)kF32BandStage * sizeof(float);
             cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_f32_band_pass<<<(unsigned)ns, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
                                                            pl->d_shadow_il.p, info, (float)pl->fp32_pivot_floor);
+            trace_mark(pl, st, "k_f32_band_pass");
             const size_t bs = (size_t)kF32BorderStage * sizeof(float);
             cudaFuncSetAttribute(k_f32_border_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
             k_f32_border_pass<<<(unsigned)ns, kBorderThreads, bs, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
                                                                        pl->d_shadow_il.p, pl->d_l21_il.p, blocks,
                                                                        info);
+            trace_mark(pl, st, "k_f32_border_pass");
             k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(
                 pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
                 pl->d_l21_il.p, blocks);
+            trace_mark(pl, st, "k_f32_out");
             // near-degenerate blocks: FP64 from the untouched FP64 input
             launch_band<ArF64>(pl, false, blocks, info, st, 1);
+            trace_mark(pl, st, "k_factor_rescue");
         }
-    } else if (precision == SYMPIX_PREC_FP32)
+    } else if (precision == SYMPIX_PREC_FP32) {
         launch_band<ArF32>(pl, dense, blocks, info, st);
-    else
+        trace_mark(pl, st, "k_factor_band");
+    } else {
         launch_band<ArF2>(pl, dense, blocks, info, st);
+        trace_mark(pl, st, "k_factor_band");
+    }
     const int nw = (int)pl->factor_items[5].size();
     if (nw) {
         const size_t smem = (size_t)((kWideMax + 1) * (kWideMax + 1) + kWideMax * (kWideMax + 1) +
@@ -1535,13 +1554,16 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
             kd<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 0, 0.0f, nullptr);
         }
     }
+    if (nw) trace_mark(pl, st, "k_factor_wide");
     const int nd = (int)pl->factor_items[3].size(), ns = (int)pl->factor_items[4].size();
     if (nd)
         k_factor_dense<<<(unsigned)((nd * 32 + 127) / 128), 128, 0, st>>>(nd, pl->d_factor_items[3].p, pl->d_blocks.p,
                                                                         blocks, dense ? 1 : 0, info);
+    if (nd) trace_mark(pl, st, "k_factor_dense");
     if (ns)
         k_factor_serial<<<(unsigned)((ns + 31) / 32), 32, 0, st>>>(ns, pl->d_factor_items[4].p, pl->d_blocks.p, blocks,
                                                                   dense ? 1 : 0, info);
+    if (ns) trace_mark(pl, st, "k_factor_serial");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_factor_blocks: launch");
     return SYMPIX_OK;

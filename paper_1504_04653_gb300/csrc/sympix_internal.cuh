@@ -23,6 +23,13 @@ int cuda_error(cudaError_t e, const char *what);
         if (e__ != cudaSuccess) return cuda_error(e__, #call); \
     } while (0)
 
+// Record a trace event on `st` (no-op unless the plan traces and `st` is not
+// capturing); `name` labels the span since the previous mark, null starts a call.
+void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
+
+// Elements per block in one CTA of the FP32 shadow transposes (x 32 blocks).
+constexpr int kTileE = 128;
+
 // Device buffer owned by a handle.
 template <typename T>
 struct DevBuf {
@@ -172,5 +179,14 @@ struct sympix_plan_s {
     sympix::DevBuf<int2> d_f32_out_tiles;
     sympix::DevBuf<float> d_shadow;     // FP32 band rows of wide blocks, at their pband offsets
     bool table_ready = false;
+    // tracing (SYMPIX_OPT_TRACE): an event after every launch of a traced
+    // call; a null name marks the start of a call
+    bool trace = false;
+    std::vector<cudaEvent_t> trace_ev;
+    std::vector<const char *> trace_name;
+    int trace_n = 0;
+    ~sympix_plan_s() {
+        for (cudaEvent_t e : trace_ev) cudaEventDestroy(e);
+    }
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
 };

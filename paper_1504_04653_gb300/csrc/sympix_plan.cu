@@ -364,9 +364,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                 sl.sh = sh;
                 sl.l21 = l21;
                 const int64_t elems = (int64_t)sl.rows * (w + 1), elems21 = (int64_t)w * (sl.rows - w);
-                for (int64_t e0 = 0; e0 < elems; e0 += 64)
+                for (int64_t e0 = 0; e0 < elems; e0 += kTileE)
                     pl->f32_tiles.push_back(make_int2((int)pl->f32_slices.size(), (int)e0));
-                for (int64_t e0 = 0; e0 < elems21; e0 += 64)
+                for (int64_t e0 = 0; e0 < elems21; e0 += kTileE)
                     tiles21.push_back(make_int2((int)pl->f32_slices.size(), (int)(-1 - e0)));
                 sh += 32 * elems;
                 l21 += 32 * elems21;
@@ -405,6 +405,8 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     return SYMPIX_OK;
 }
 
+constexpr int kTraceCap = 256;
+
 extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_option: NULL plan");
     if (option == SYMPIX_OPT_FP32_PIVOT_FLOOR) {
@@ -413,7 +415,47 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         pl->fp32_pivot_floor = value;
         return SYMPIX_OK;
     }
+    if (option == SYMPIX_OPT_TRACE) {
+        if (value != 0.0 && value != 1.0) return set_error(SYMPIX_EINVAL, "sympix_plan_option: trace is 0 or 1");
+        if (value == 1.0 && pl->trace_ev.empty()) {
+            pl->trace_ev.resize(kTraceCap, nullptr);
+            pl->trace_name.resize(kTraceCap, nullptr);
+            for (auto &e : pl->trace_ev) SPX_CUDA(cudaEventCreate(&e));
+        }
+        pl->trace = value == 1.0;
+        pl->trace_n = 0;
+        return SYMPIX_OK;
+    }
     return set_error(SYMPIX_EINVAL, "sympix_plan_option: unknown option %d", option);
+}
+
+namespace sympix {
+void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name) {
+    if (!pl->trace || pl->trace_n >= kTraceCap) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventRecord(pl->trace_ev[pl->trace_n], st) != cudaSuccess) return;
+    pl->trace_name[pl->trace_n++] = name;
+}
+}  // namespace sympix
+
+extern "C" int sympix_trace_read(sympix_plan_t pl, int cap, const char **names, float *ms, int *count) {
+    if (!pl || !count || (cap > 0 && (!names || !ms))) return set_error(SYMPIX_EINVAL, "sympix_trace_read: NULL argument");
+    int k = 0;
+    if (pl->trace_n > 0) SPX_CUDA(cudaEventSynchronize(pl->trace_ev[pl->trace_n - 1]));
+    for (int i = 1; i < pl->trace_n; ++i) {
+        if (!pl->trace_name[i]) continue;
+        if (k < cap) {
+            float t = 0.0f;
+            SPX_CUDA(cudaEventElapsedTime(&t, pl->trace_ev[i - 1], pl->trace_ev[i]));
+            names[k] = pl->trace_name[i];
+            ms[k] = t;
+        }
+        ++k;
+    }
+    *count = k;
+    pl->trace_n = 0;
+    return SYMPIX_OK;
 }
 
 extern "C" int sympix_plan_counts(sympix_plan_t pl, int64_t *nslots, int64_t *npairs, int64_t *ntriples,

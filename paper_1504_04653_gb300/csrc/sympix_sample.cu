@@ -93,10 +93,12 @@ extern "C" int sympix_sample_blocks(sympix_plan_t pl, const double *ninv, int pr
         return set_error(SYMPIX_EINVAL, "sympix_sample_blocks: sympix_kernel_table has not been called");
     cudaStream_t st = (cudaStream_t)stream;
     const bool dense = storage == SYMPIX_STORE_DENSE;
+    trace_mark(pl, st, nullptr);
     if (dense) SPX_CUDA(cudaMemsetAsync(blocks, 0, (size_t)pl->size_dense * sizeof(double), st));
     if (precision != SYMPIX_PREC_FP64) {
         const int64_t cnt = (int64_t)pl->nops * pl->grid->npix;
         k_split_ninv<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ninv, pl->d_ninv32.p, pl->d_ninvlo.p);
+        trace_mark(pl, st, "k_split_ninv");
     }
     if (precision == SYMPIX_PREC_FP64) {
         dense ? launch_pband<0, true>(pl, ninv, blocks, st) : launch_pband<0, false>(pl, ninv, blocks, st);
@@ -105,10 +107,12 @@ extern "C" int sympix_sample_blocks(sympix_plan_t pl, const double *ninv, int pr
     } else {
         dense ? launch_pband<2, true>(pl, ninv, blocks, st) : launch_pband<2, false>(pl, ninv, blocks, st);
     }
+    trace_mark(pl, st, "k_sample_pband");
     if (!pl->items_dense.empty())
         k_sample_dense<<<(unsigned)pl->items_dense.size(), 256, 0, st>>>(
             pl->d_items_dense.p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, pl->grid->npix, pl->d_tab_b.p,
             pl->d_tab_d.p, ninv, blocks, dense ? 1 : 0);
+    trace_mark(pl, st, "k_sample_dense");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_sample_blocks: launch");
     return SYMPIX_OK;

@@ -30,10 +30,14 @@ __global__ void k_table_coeffs(int lmax, int nops, const double *__restrict__ bl
     }
 }
 
-// One thread per slot; the same-ring slots also get d.  nops operators are
-// summed from one pass of the recurrence.
+// kTableSpt slots per thread, kTableCta threads per CTA; the same-ring slots
+// also get d.  nops operators are summed from one pass of the recurrence.
+// The kernel is bound by each SM's FP64 pipe, so what matters is an even
+// spread: small CTAs give every SM nearly the same number of slots.
+constexpr int kTableSpt = 1, kTableCta = 32;
+
 template <int NOPS>
-__global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, int op0, int lmax,
+__global__ void __launch_bounds__(kTableCta) k_table(int64_t nslots, int nops_total, int op0, int lmax,
                                                const double *__restrict__ slot_u,
                                                const int32_t *__restrict__ slot_pair,
                                                const CanonPair *__restrict__ pairs,
@@ -42,57 +46,78 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
                                                double *__restrict__ td, float *__restrict__ tb32,
                                                float *__restrict__ tblo, float *__restrict__ td32,
                                                float *__restrict__ tdlo) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nslots) return;
-    const double u = slot_u[s];
-    const CanonPair cp = pairs[slot_pair[s]];
-    const bool same = cp.a == cp.b;
+    constexpr int J = kTableSpt;
     const int L1 = lmax + 1;
     const int nops = min(NOPS, nops_total - op0);
-    double sb[NOPS], sd[NOPS];
-    double p = 1.0, dlt = -u;
+    int64_t s[J];
+    bool ok[J], same[J];
+    double u[J], p[J], dlt[J], sb[J][NOPS], sd[J][NOPS];
 #pragma unroll
-    for (int o = 0; o < NOPS; ++o) {
-        sb[o] = 0.0;
-        sd[o] = 0.0;
-        if (o < nops) {
-            sb[o] = cb[(op0 + o) * L1];
-            if (same) sd[o] = cd[(op0 + o) * L1];
+    for (int j = 0; j < J; ++j) {
+        s[j] = ((int64_t)blockIdx.x * J + j) * blockDim.x + threadIdx.x;
+        ok[j] = s[j] < nslots;
+        u[j] = ok[j] ? slot_u[s[j]] : 0.0;
+        same[j] = ok[j] && pairs[slot_pair[s[j]]].a == pairs[slot_pair[s[j]]].b;
+        p[j] = 1.0;
+        dlt[j] = -u[j];
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o) {
+            sb[j][o] = 0.0;
+            sd[j][o] = 0.0;
+            if (o < nops) {
+                sb[j][o] = cb[(op0 + o) * L1];
+                if (same[j]) sd[j][o] = cd[(op0 + o) * L1];
+            }
         }
     }
     if (lmax >= 1) {
-        p = 1.0 - u;
 #pragma unroll
-        for (int o = 0; o < NOPS; ++o)
-            if (o < nops) {
-                sb[o] = fma(cb[(op0 + o) * L1 + 1], p, sb[o]);
-                if (same) sd[o] = fma(cd[(op0 + o) * L1 + 1], p, sd[o]);
-            }
+        for (int j = 0; j < J; ++j) {
+            p[j] = 1.0 - u[j];
+#pragma unroll
+            for (int o = 0; o < NOPS; ++o)
+                if (o < nops) {
+                    sb[j][o] = fma(cb[(op0 + o) * L1 + 1], p[j], sb[j][o]);
+                    if (same[j]) sd[j][o] = fma(cd[(op0 + o) * L1 + 1], p[j], sd[j][o]);
+                }
+        }
     }
     for (int l = 1; l < lmax; ++l) {  // dlt = E_l on entry (E_1 = -u)
-        dlt = fma(rec[2 * l], u * p, dlt);
-        p = fma(dlt, rec[2 * l + 1], p);
+        const double a = rec[2 * l], r = rec[2 * l + 1];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            dlt[j] = fma(a, u[j] * p[j], dlt[j]);
+            p[j] = fma(dlt[j], r, p[j]);
+        }
 #pragma unroll
         for (int o = 0; o < NOPS; ++o)
             if (o < nops) {
-                sb[o] = fma(cb[(op0 + o) * L1 + l + 1], p, sb[o]);
-                if (same) sd[o] = fma(cd[(op0 + o) * L1 + l + 1], p, sd[o]);
+                const double c = cb[(op0 + o) * L1 + l + 1], e = cd[(op0 + o) * L1 + l + 1];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    sb[j][o] = fma(c, p[j], sb[j][o]);
+                    if (same[j]) sd[j][o] = fma(e, p[j], sd[j][o]);
+                }
             }
     }
 #pragma unroll
-    for (int o = 0; o < NOPS; ++o)
-        if (o < nops) {
-            const int64_t idx = (int64_t)(op0 + o) * nslots + s;
-            tb[idx] = sb[o];
-            td[idx] = same ? sd[o] : 0.0;
-            const float hi = (float)sb[o];
-            tb32[idx] = hi;
-            tblo[idx] = (float)(sb[o] - (double)hi);
-            const double dv = same ? sd[o] : 0.0;
-            const float dh = (float)dv;
-            td32[idx] = dh;
-            tdlo[idx] = (float)(dv - (double)dh);
-        }
+    for (int j = 0; j < J; ++j) {
+        if (!ok[j]) continue;
+#pragma unroll
+        for (int o = 0; o < NOPS; ++o)
+            if (o < nops) {
+                const int64_t idx = (int64_t)(op0 + o) * nslots + s[j];
+                tb[idx] = sb[j][o];
+                td[idx] = same[j] ? sd[j][o] : 0.0;
+                const float hi = (float)sb[j][o];
+                tb32[idx] = hi;
+                tblo[idx] = (float)(sb[j][o] - (double)hi);
+                const double dv = same[j] ? sd[j][o] : 0.0;
+                const float dh = (float)dv;
+                td32[idx] = dh;
+                tdlo[idx] = (float)(dv - (double)dh);
+            }
+    }
 }
 
 }  // namespace sympix
@@ -112,14 +137,16 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
     double *cb = rec + 2 * L1;
     double *cd = cb + (size_t)pl->nops * L1;
     const int tot = pl->nops * L1;
+    trace_mark(pl, st, nullptr);
     k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
+    trace_mark(pl, st, "k_table_coeffs");
     if (pl->nslots > 0) {
-        const unsigned grid = (unsigned)((pl->nslots + 127) / 128);
+        const unsigned grid = (unsigned)((pl->nslots + kTableCta * kTableSpt - 1) / (kTableCta * kTableSpt));
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
             const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define SPX_TABLE(NO)                                                                                              \
-    k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+    k_table<NO><<<grid, kTableCta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
                                       pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)
@@ -132,6 +159,7 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
             op0 += chunk;
         }
     }
+    trace_mark(pl, st, "k_table");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table: launch");
     pl->table_ready = true;
@@ -213,12 +241,12 @@ extern "C" int sympix_kernel_table_static(sympix_plan_t pl, const double *bl, co
     // every scratch entry read below is written first by k_table_coeffs
     k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
     if (pl->nslots > 0) {
-        const unsigned grid = (unsigned)((pl->nslots + 127) / 128);
+        const unsigned grid = (unsigned)((pl->nslots + kTableCta * kTableSpt - 1) / (kTableCta * kTableSpt));
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
             const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define SPX_TABLE_S(NO)                                                                                            \
-    k_table<NO><<<grid, 128, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+    k_table<NO><<<grid, kTableCta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
                                       pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)

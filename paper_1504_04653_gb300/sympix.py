@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
-OPT_FP32_PIVOT_FLOOR = 1
+OPT_FP32_PIVOT_FLOOR, OPT_TRACE = 1, 2
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
@@ -65,6 +65,7 @@ SIGNATURES = [
     ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
     ("sympix_factor_blocks", _i, [_vp, _i, _i, _vp, _vp, _vp]),
+    ("sympix_trace_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), _i32p]),
     ("sympix_plan_free", None, [_vp]),
     ("sympix_step_create", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_vp)]),
     ("sympix_step_launch", _i, [_vp, _i, _vp]),
@@ -190,6 +191,19 @@ class Plan:
     def set_pivot_floor(self, value: float):
         """FP32 factor: blocks whose pivots shrink below value x diagonal go to FP64."""
         _check(lib().sympix_plan_option(self._h, OPT_FP32_PIVOT_FLOOR, float(value)))
+
+    def set_trace(self, on: bool):
+        """Record a CUDA event after every kernel launch of direct calls."""
+        _check(lib().sympix_plan_option(self._h, OPT_TRACE, 1.0 if on else 0.0))
+
+    def trace_read(self):
+        """[(kernel name, ms), ...] of the traced launches since the last read."""
+        cap = 256
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_float * cap)()
+        cnt = ctypes.c_int32()
+        _check(lib().sympix_trace_read(self._h, cap, names, ms, ctypes.byref(cnt)))
+        return [(names[i].decode(), float(ms[i])) for i in range(min(cnt.value, cap))]
 
     def launches(self, storage="pband", sample_precision="fp32", factor_precision="fp32"):
         """Kernel launches of (kernel_table, sample_blocks, factor_blocks)."""

@@ -101,3 +101,23 @@ def test_step_rejects_bad_arguments():
             step.launch(bad)
     with pytest.raises(S.SympixError):
         S.Step(plan, bl, dl, ninv, blocks[:10], info)
+
+
+def test_trace_names_every_kernel():
+    """SYMPIX_OPT_TRACE: one span per kernel launch group, positive times,
+    nothing recorded once tracing is off."""
+    wl, grid, plan, colat, bl, dl, ninv = _setup("lmax500")
+    plan.set_trace(True)
+    S.sympix_kernel_table(plan, bl, dl)
+    blocks = S.sympix_sample_blocks(plan, ninv, precision="fp32", storage="pband")
+    S.sympix_factor_blocks(plan, blocks, storage="pband", precision="fp32")
+    spans = plan.trace_read()
+    names = [n for n, _ in spans]
+    for k in ("k_table", "k_split_ninv", "k_sample_pband", "k_f32_shadow_in", "k_f32_band_pass",
+              "k_f32_border_pass", "k_f32_out"):
+        assert k in names, names
+    assert all(ms >= 0.0 for _, ms in spans)
+    assert plan.trace_read() == []
+    plan.set_trace(False)
+    S.sympix_kernel_table(plan, bl, dl)
+    assert plan.trace_read() == []
