@@ -47,6 +47,7 @@ def parse():
                     help="headline arithmetic as contraction:factor (fp64, fp32x2 or fp32 each)")
     ap.add_argument("--launch", default="graph", choices=["graph", "eager"],
                     help="replay the step as captured CUDA graphs, or call the entry points directly")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--arms", default="fp64:fp64,fp32x2:fp32x2",
@@ -164,7 +165,12 @@ ALU_PEAK = {"fp64": (FP64_NOMINAL, "nominal FP64 1.25 TFLOP/s (a DFMA probe meas
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of (workload, precision), as summarised under
 # profiles/; an entry is removed when its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/dram_lmax3000_mixed_step.md: 472.2 MB read + 371.6 MB written
+    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_border_pass"): 843817472,
+    ("lmax3000_fwhm5", "fp32:fp32", "k_table"): 799744,
+    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_band_pass"): 853650944,
+}
 
 
 def kernel_work(plan, grid, wl, elements, sprec, fprec):
@@ -254,6 +260,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
+    # launch shapes: timed on this workload before anything is captured
+    tune = None
+    if not args.no_autotune:
+        sp0, fp0 = args.precision.split(":")
+        tune = plan.autotune(bl, dl, ninv, blocks, info, "pband", sp0, fp0, stream=stream)
+        torch.cuda.synchronize()
     graphs = {}
 
     def graph_step(prec):
@@ -469,6 +481,8 @@ def main():
                    "precision": args.precision, "triples": int(plan.ntriples), "kernel_slots": int(plan.nslots),
                    "l2": "256 MB buffer written between steps, outside the step events",
                    "launch": "one CUDA graph replay per stage" if args.launch == "graph" else "direct calls",
+                   "launch_shapes": {"table_cta": plan.tuning()[0], "border_threads": plan.tuning()[1],
+                                     "autotuned": tune is not None},
                    "parallelism": f"independent problem per GPU x{world}"},
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "kernel_rooflines": kernels,

@@ -141,9 +141,27 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
 #define SYMPIX_OPT_TRACE 2            /* 1: record a CUDA event after every kernel launch of
                                           sympix_kernel_table / _sample_blocks / _factor_blocks
                                           (direct calls, not stream capture); 0: off (default) */
+#define SYMPIX_OPT_TABLE_CTA 3        /* threads per CTA of the kernel-table launch: 32, 64 or
+                                          128 (default 32) */
+#define SYMPIX_OPT_BORDER_THREADS 4   /* threads per CTA of the FP32 border pass: 256 or 512
+                                          (default 512) */
 
 /* Set a plan option; takes effect for the following calls on the plan. */
 int sympix_plan_option(sympix_plan_t plan, int option, double value);
+
+/* Autotune the launch shapes (SYMPIX_OPT_TABLE_CTA, SYMPIX_OPT_BORDER_THREADS)
+ * on the caller's data: each candidate runs the calls it affects
+ * (sympix_kernel_table with bl, dl; sympix_sample_blocks and
+ * sympix_factor_blocks with ninv, storage, the precisions, blocks and info)
+ * once to warm up and once timed with CUDA events on `stream`; the fastest is
+ * kept in the plan.  Results are identical for every candidate; blocks and
+ * info are overwritten.  Synchronous.  The paper has no counterpart: this
+ * chooses how the same operations are launched. */
+int sympix_autotune(sympix_plan_t plan, const double *bl, const double *dl, const double *ninv, int storage,
+                    int sample_precision, int factor_precision, double *blocks, int32_t *info, void *stream);
+
+/* The plan's launch shapes (either pointer may be NULL). */
+int sympix_plan_tuning(sympix_plan_t plan, int *table_cta, int *border_threads);
 
 /* Per-kernel device times of the traced calls since the last read
  * (SYMPIX_OPT_TRACE): waits for the last recorded event, then writes up to

@@ -1054,23 +1054,20 @@ __device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice
     __syncthreads();
 }
 
-// One CTA of kBorderThreads per slice: one border row per warp.
-constexpr int kBorderThreads = 512;
-
-__global__ void __launch_bounds__(kBorderThreads) k_f32_border_pass(const F32Slice *__restrict__ slices,
-                                                                    const int32_t *__restrict__ items,
-                                                                    const BlockDesc *__restrict__ blocks,
-                                                                    const float *__restrict__ sh,
-                                                                    float *__restrict__ l21,
-                                                                    const double *__restrict__ out,
-                                                                    int32_t *__restrict__ info) {
+// One CTA of NT threads per slice (256 or 512, the plan's border_threads):
+// warp q owns border rows R q .. R q + R-1, R = ceil(w / (NT / 32)).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_f32_border_pass(const F32Slice *__restrict__ slices,
+                                                        const int32_t *__restrict__ items,
+                                                        const BlockDesc *__restrict__ blocks,
+                                                        const float *__restrict__ sh, float *__restrict__ l21,
+                                                        const double *__restrict__ out, int32_t *__restrict__ info) {
     extern __shared__ __align__(16) float bsm[];
     __shared__ SliceBlocks t;
     __shared__ int binfo[32];
     const F32Slice sl = slices[blockIdx.x];
     load_slice_blocks(t, sl, items, blocks, info);
-    F32BorderDispatch<16, 1, kBorderThreads>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm,
-                                                  binfo);
+    F32BorderDispatch<16, 1, NT>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm, binfo);
     if (threadIdx.x < 32 && t.live[threadIdx.x] && sl.w > 0) info[t.bi[threadIdx.x]] = binfo[threadIdx.x];
 }
 
@@ -1512,10 +1509,10 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
                                                            pl->d_shadow_il.p, info, (float)pl->fp32_pivot_floor);
             trace_mark(pl, st, "k_f32_band_pass");
             const size_t bs = (size_t)kF32BorderStage * sizeof(float);
-            cudaFuncSetAttribute(k_f32_border_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
-            k_f32_border_pass<<<(unsigned)ns, kBorderThreads, bs, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
-                                                                       pl->d_shadow_il.p, pl->d_l21_il.p, blocks,
-                                                                       info);
+            auto kb = pl->border_threads == 256 ? k_f32_border_pass<256> : k_f32_border_pass<512>;
+            cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
+            kb<<<(unsigned)ns, pl->border_threads, bs, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow_il.p,
+                                                            pl->d_l21_il.p, blocks, info);
             trace_mark(pl, st, "k_f32_border_pass");
             k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(
                 pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,

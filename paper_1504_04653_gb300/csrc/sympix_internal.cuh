@@ -181,6 +181,7 @@ struct sympix_plan_s {
     bool table_ready = false;
     // tracing (SYMPIX_OPT_TRACE): an event after every launch of a traced
     // call; a null name marks the start of a call
+    int table_cta = 32, border_threads = 512;  // launch shapes (autotuned)
     bool trace = false;
     std::vector<cudaEvent_t> trace_ev;
     std::vector<const char *> trace_name;

@@ -415,6 +415,18 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         pl->fp32_pivot_floor = value;
         return SYMPIX_OK;
     }
+    if (option == SYMPIX_OPT_TABLE_CTA) {
+        if (value != 32.0 && value != 64.0 && value != 128.0)
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: table CTA size is 32, 64 or 128");
+        pl->table_cta = (int)value;
+        return SYMPIX_OK;
+    }
+    if (option == SYMPIX_OPT_BORDER_THREADS) {
+        if (value != 256.0 && value != 512.0)
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: border threads are 256 or 512");
+        pl->border_threads = (int)value;
+        return SYMPIX_OK;
+    }
     if (option == SYMPIX_OPT_TRACE) {
         if (value != 0.0 && value != 1.0) return set_error(SYMPIX_EINVAL, "sympix_plan_option: trace is 0 or 1");
         if (value == 1.0 && pl->trace_ev.empty()) {
@@ -438,6 +450,75 @@ void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name) {
     pl->trace_name[pl->trace_n++] = name;
 }
 }  // namespace sympix
+
+extern "C" int sympix_plan_tuning(sympix_plan_t pl, int *table_cta, int *border_threads) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_tuning: NULL plan");
+    if (table_cta) *table_cta = pl->table_cta;
+    if (border_threads) *border_threads = pl->border_threads;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_autotune(sympix_plan_t pl, const double *bl, const double *dl, const double *ninv, int storage,
+                               int sample_precision, int factor_precision, double *blocks, int32_t *info,
+                               void *stream) {
+    if (!pl || !bl || !dl || !ninv || !blocks || !info) return set_error(SYMPIX_EINVAL, "sympix_autotune: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    SPX_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_error(ce, "sympix_autotune: cudaEventCreate");
+    }
+    const bool tr = pl->trace;
+    pl->trace = false;
+    int rc = SYMPIX_OK;
+    // time `run` once after one warm-up call
+    auto timed = [&](auto run, float *ms) -> int {
+        int r = run();
+        if (r) return r;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return set_error(SYMPIX_ECUDA, "sympix_autotune: event");
+        if ((r = run())) return r;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return set_error(SYMPIX_ECUDA, "sympix_autotune: event timing");
+        return SYMPIX_OK;
+    };
+    float best = 1e30f;
+    int best_cta = pl->table_cta;
+    for (int cta : {32, 64, 128}) {
+        pl->table_cta = cta;
+        float ms = 0.0f;
+        if ((rc = timed([&] { return sympix_kernel_table(pl, bl, dl, st); }, &ms))) break;
+        if (ms < best) {
+            best = ms;
+            best_cta = cta;
+        }
+    }
+    pl->table_cta = best_cta;
+    if (!rc && factor_precision == SYMPIX_PREC_FP32 && storage == SYMPIX_STORE_PBAND && !pl->f32_slices.empty()) {
+        best = 1e30f;
+        int best_nt = pl->border_threads;
+        for (int nt : {256, 512}) {
+            pl->border_threads = nt;
+            float ms = 0.0f;
+            auto run = [&] {
+                int r = sympix_sample_blocks(pl, ninv, sample_precision, storage, blocks, st);
+                return r ? r : sympix_factor_blocks(pl, storage, factor_precision, blocks, info, st);
+            };
+            if ((rc = timed(run, &ms))) break;
+            if (ms < best) {
+                best = ms;
+                best_nt = nt;
+            }
+        }
+        pl->border_threads = best_nt;
+    }
+    pl->trace = tr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
 
 extern "C" int sympix_trace_read(sympix_plan_t pl, int cap, const char **names, float *ms, int *count) {
     if (!pl || !count || (cap > 0 && (!names || !ms))) return set_error(SYMPIX_EINVAL, "sympix_trace_read: NULL argument");

@@ -30,14 +30,15 @@ __global__ void k_table_coeffs(int lmax, int nops, const double *__restrict__ bl
     }
 }
 
-// kTableSpt slots per thread, kTableCta threads per CTA; the same-ring slots
-// also get d.  nops operators are summed from one pass of the recurrence.
-// The kernel is bound by each SM's FP64 pipe, so what matters is an even
-// spread: small CTAs give every SM nearly the same number of slots.
-constexpr int kTableSpt = 1, kTableCta = 32;
+// kTableSpt slots per thread, blockDim.x (the plan's table_cta: 32, 64 or
+// 128) threads per CTA; the same-ring slots also get d.  nops operators are
+// summed from one pass of the recurrence.  The kernel is bound by each SM's
+// FP64 pipe, so what matters is an even spread: small CTAs give every SM
+// nearly the same number of slots.
+constexpr int kTableSpt = 1;
 
 template <int NOPS>
-__global__ void __launch_bounds__(kTableCta) k_table(int64_t nslots, int nops_total, int op0, int lmax,
+__global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, int op0, int lmax,
                                                const double *__restrict__ slot_u,
                                                const int32_t *__restrict__ slot_pair,
                                                const CanonPair *__restrict__ pairs,
@@ -141,12 +142,13 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
     k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
     trace_mark(pl, st, "k_table_coeffs");
     if (pl->nslots > 0) {
-        const unsigned grid = (unsigned)((pl->nslots + kTableCta * kTableSpt - 1) / (kTableCta * kTableSpt));
+        const int cta = pl->table_cta;
+        const unsigned grid = (unsigned)((pl->nslots + cta * kTableSpt - 1) / (cta * kTableSpt));
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
             const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define SPX_TABLE(NO)                                                                                              \
-    k_table<NO><<<grid, kTableCta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+    k_table<NO><<<grid, cta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
                                       pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)
@@ -241,12 +243,13 @@ extern "C" int sympix_kernel_table_static(sympix_plan_t pl, const double *bl, co
     // every scratch entry read below is written first by k_table_coeffs
     k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
     if (pl->nslots > 0) {
-        const unsigned grid = (unsigned)((pl->nslots + kTableCta * kTableSpt - 1) / (kTableCta * kTableSpt));
+        const int cta = pl->table_cta;
+        const unsigned grid = (unsigned)((pl->nslots + cta * kTableSpt - 1) / (cta * kTableSpt));
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
             const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define SPX_TABLE_S(NO)                                                                                            \
-    k_table<NO><<<grid, kTableCta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
+    k_table<NO><<<grid, cta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
                                       pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
             if (chunk == 4)

@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
-OPT_FP32_PIVOT_FLOOR, OPT_TRACE = 1, 2
+OPT_FP32_PIVOT_FLOOR, OPT_TRACE, OPT_TABLE_CTA, OPT_BORDER_THREADS = 1, 2, 3, 4
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
@@ -65,6 +65,8 @@ SIGNATURES = [
     ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
     ("sympix_factor_blocks", _i, [_vp, _i, _i, _vp, _vp, _vp]),
+    ("sympix_autotune", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
+    ("sympix_plan_tuning", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     ("sympix_trace_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), _i32p]),
     ("sympix_plan_free", None, [_vp]),
     ("sympix_step_create", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -191,6 +193,27 @@ class Plan:
     def set_pivot_floor(self, value: float):
         """FP32 factor: blocks whose pivots shrink below value x diagonal go to FP64."""
         _check(lib().sympix_plan_option(self._h, OPT_FP32_PIVOT_FLOOR, float(value)))
+
+    def set_launch_shape(self, table_cta=None, border_threads=None):
+        """Launch shapes: table CTA size (32, 64, 128), FP32 border-pass threads (256, 512)."""
+        if table_cta is not None:
+            _check(lib().sympix_plan_option(self._h, OPT_TABLE_CTA, float(table_cta)))
+        if border_threads is not None:
+            _check(lib().sympix_plan_option(self._h, OPT_BORDER_THREADS, float(border_threads)))
+
+    def tuning(self):
+        """(table CTA size, border-pass threads) the plan launches with."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().sympix_plan_tuning(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, bl, dl, ninv, blocks, info, storage="pband", sample_precision="fp32",
+                 factor_precision="fp32", stream=None):
+        """Time the launch-shape candidates on these buffers and keep the fastest."""
+        _check(lib().sympix_autotune(self._h, _ptr(bl), _ptr(dl), _ptr(ninv), STORAGES[storage],
+                                     PRECISIONS[sample_precision], PRECISIONS[factor_precision], _ptr(blocks),
+                                     _ptr(info), _stream(stream)))
+        return self.tuning()
 
     def set_trace(self, on: bool):
         """Record a CUDA event after every kernel launch of direct calls."""

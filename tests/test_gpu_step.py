@@ -121,3 +121,28 @@ def test_trace_names_every_kernel():
     plan.set_trace(False)
     S.sympix_kernel_table(plan, bl, dl)
     assert plan.trace_read() == []
+
+
+def test_launch_shapes_agree_and_autotune():
+    """Every launch shape gives the same blocks and factors, bit for bit; the
+    autotuner keeps one of the candidates."""
+    wl, grid, plan, colat, bl, dl, ninv = _setup("lmax500")
+    nbytes, _ = plan.blocks_size("pband")
+    ref = None
+    for cta, nt in ((32, 512), (64, 256), (128, 512)):
+        plan.set_launch_shape(table_cta=cta, border_threads=nt)
+        assert plan.tuning() == (cta, nt)
+        got = _direct(plan, bl, dl, ninv, "pband", "fp32", "fp32")
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b)
+    blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
+    info = torch.empty(plan.nblocks, dtype=torch.int32, device="cuda")
+    cta, nt = plan.autotune(bl, dl, ninv, blocks, info)
+    assert cta in (32, 64, 128) and nt in (256, 512)
+    with pytest.raises(S.SympixError):
+        plan.set_launch_shape(table_cta=48)
+    with pytest.raises(S.SympixError):
+        plan.set_launch_shape(border_threads=384)
