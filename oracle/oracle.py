@@ -63,6 +63,9 @@ def lib():
                                           ctypes.c_int, _dptr, _dptr, ctypes.c_double,
                                           _dptr, ctypes.c_int, _dptr]
         L.sympix_oracle_cholesky.argtypes = [ctypes.c_int, _dptr, _dptr]
+        L.sympix_oracle_convolve.restype = ctypes.c_long
+        L.sympix_oracle_convolve.argtypes = [ctypes.c_int, _dptr, _i32ptr, _i64ptr, _i32ptr, ctypes.c_int, _dptr,
+                                             ctypes.c_double, _dptr, ctypes.c_int, _i32ptr, _i32ptr, _dptr]
         L.sympix_oracle_ordering.restype = ctypes.c_long
         L.sympix_oracle_ordering.argtypes = [ctypes.c_int, ctypes.c_int, _i32ptr, _i64ptr, _i32ptr]
         _lib = L
@@ -199,6 +202,26 @@ def block(g: dict, bl: np.ndarray, dl: np.ndarray, r_s: float, ninv: np.ndarray,
                                         _p(b, _dptr), _p(d, _dptr), float(r_s),
                                         _p(nv, _dptr), int(j), _p(M, _dptr))
     return M, int(triples)
+
+
+def convolve(g: dict, bl: np.ndarray, r_s: float, f: np.ndarray, q_ring, q_col):
+    """Pixel-domain convolution g_q = sum_p b(n_q . n_p) f_p over the pixels
+    within r_s (Eq. convolution-pixel), at the pixels (q_ring[i], q_col[i]);
+    returns (g, number of coupled pairs summed)."""
+    qr = np.ascontiguousarray(q_ring, dtype=np.int32)
+    qc = np.ascontiguousarray(q_col, dtype=np.int32)
+    out = np.zeros(len(qr))
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    off = np.ascontiguousarray(g["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g["ring_stride"], dtype=np.int32)
+    b = _f64(bl)
+    fv = _f64(f)
+    assert len(fv) == g["npix"]
+    pairs = lib().sympix_oracle_convolve(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), _p(off, _i64ptr),
+                                         _p(st, _i32ptr), g["lmax"], _p(b, _dptr), float(r_s), _p(fv, _dptr),
+                                         len(qr), _p(qr, _i32ptr), _p(qc, _i32ptr), _p(out, _dptr))
+    return out, int(pairs)
 
 
 def cholesky(A: np.ndarray):

@@ -361,6 +361,44 @@ long sympix_oracle_block(int nrings, const double *theta, const int32_t *nring,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pixel-domain convolution (Eq. convolution-pixel)                          */
+/* ------------------------------------------------------------------------ */
+
+/* g at nq output pixels (ring q_ring[i], column q_col[i]):
+ *   g_i = sum over every pixel p of every ring with u_ip <= u_s of
+ *         b(1 - u_ip) f_p,
+ * b by Eq. addition-theorem with coefficients bl, truncated at the radius r_s
+ * (the approximation b = 0 beyond the support, Sec. 3).  f is indexed by the
+ * grid's pixel numbering (pixel c of ring r is ring_offset[r] +
+ * c * ring_stride[r]).  Returns the number of coupled pairs summed. */
+long sympix_oracle_convolve(int nrings, const double *theta, const int32_t *nring,
+                            const int64_t *ring_offset, const int32_t *ring_stride,
+                            int lmax, const double *bl, double r_s, const double *f,
+                            int nq, const int32_t *q_ring, const int32_t *q_col, double *g)
+{
+    double us = support_u(r_s);
+    long pairs = 0;
+    for (int i = 0; i < nq; ++i) {
+        int j = q_ring[i];
+        double acc = 0.0;
+        for (int rho = 0; rho < nrings; ++rho) {
+            double a = sin(0.5 * (theta[j] - theta[rho]));
+            if (2.0 * a * a > us) continue; /* no pixel of this ring is close enough */
+            for (long p = 0; p < nring[rho]; ++p) {
+                double u = sympix_oracle_u(theta[j], nring[j], q_col[i], theta[rho], nring[rho], p);
+                if (u <= us) {
+                    acc += sympix_oracle_kernel_u(lmax, bl, u) *
+                           f[ring_offset[rho] + p * (int64_t)ring_stride[rho]];
+                    ++pairs;
+                }
+            }
+        }
+        g[i] = acc;
+    }
+    return pairs;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Cholesky                                                                  */
 /* ------------------------------------------------------------------------ */
 
