@@ -464,6 +464,33 @@ def main():
             kernels[name] = {"ms": round(ms, 4), "bound": "alu", "tflops": a / (ms * 1e-3) / 1e12,
                              "frac": a / (ms * 1e-3) / ALU_PEAK[t][0]}
 
+    # the pixel-domain convolution g = B^ f on the same plan and table (the
+    # N^-1 map stands in for f): FP32 against HBM, FP64 against the FP64 pipe
+    conv = {}
+    gbuf = torch.empty_like(ninv)
+    S.sympix_kernel_table(plan, bl, dl, stream=stream)
+    for cp in ("fp32", "fp64"):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                S.sympix_convolve(plan, ninv, precision=cp, out=gbuf, stream=stream)
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                S.sympix_convolve(plan, ninv, precision=cp, out=gbuf, stream=stream)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        px = grid.npix * plan.nops
+        ent = {"ms": ms, "pixels_per_s": px / (ms * 1e-3)}
+        if cp == "fp32":
+            ent.update({"bound": "hbm", "gbs": px * 16.0 / (ms * 1e-3) / 1e9,
+                        "frac": px * 16.0 / (ms * 1e-3) / hbm})
+        else:
+            ent.update({"bound": "alu", "tflops": 2.0 * plan.nmults / (ms * 1e-3) / 1e12,
+                        "frac": 2.0 * plan.nmults / (ms * 1e-3) / FP64_NOMINAL})
+        conv[cp] = ent
+
     if args.launch == "graph":
         launches = graph_step(args.precision).kernels(S.STAGE_ALL)
     else:
@@ -487,6 +514,8 @@ def main():
         "stages_ms": {k: round(v, 4) for k, v in stages.items()},
         "kernel_rooflines": kernels,
         "arms": arms, "accuracy": acc, "roofline": roof, "e2e": e2e,
+        "convolution": {"op": "g = B^ f, pixel domain (Eq. convolution-pixel); 16 B algorithmic per pixel",
+                        **conv},
         "gpu_launches": launches * args.steps, "clocks": clk,
         "blocks": int(plan.nblocks),
         "blocks_not_positive_definite": not_pd or int((info_h != 0).sum()),

@@ -285,6 +285,18 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
 int sympix_factor_blocks(sympix_plan_t plan, int storage, int precision, double *blocks, int32_t *info,
                          void *stream);
 
+/* Pixel-domain convolution (Eq. convolution-pixel) of every operator's map
+ * with its own kernel b (Eq. addition-theorem, from sympix_kernel_table),
+ * truncated at the operator's radius r_s:
+ *   g_q = sum over the pixels p with gamma_qp <= r_s of b(n_q . n_p) f_p.
+ *   f, g       device FP64 [nops][npix] in the grid's pixel numbering; g is
+ *              written at the pixels of the planned rings [ring0, ring1).
+ *   precision  SYMPIX_PREC_*: arithmetic of the sums (FP64, FP32, or split
+ *              FP32); f is split into FP32 planes in the plan's scratch, so
+ *              calls on one plan must not overlap on the GPU.
+ * Asynchronous. */
+int sympix_convolve(sympix_plan_t plan, const double *f, int precision, double *g, void *stream);
+
 void sympix_plan_free(sympix_plan_t plan);
 
 /* ------------------------------------------------------------------------ */

@@ -30,6 +30,10 @@ void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
 // Elements per block in one CTA of the FP32 shadow transposes (x 32 blocks).
 constexpr int kTileE = 128;
 
+// FP64 [count] -> FP32 hi and lo planes (integer-ALU split; sympix_sample.cu).
+__global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, float *__restrict__ n32,
+                             float *__restrict__ nlo);
+
 // Device buffer owned by a handle.
 template <typename T>
 struct DevBuf {
@@ -127,6 +131,14 @@ struct F32Slice {
     int64_t sh, l21;
 };
 
+// One tile of the pixel-domain convolution: pixels q0 .. q0+127 of block
+// `block`'s ring, whose column c is output pixel goff + c * gstride.
+struct ConvItem {
+    int32_t block, q0;
+    int64_t goff;
+    int32_t gstride, pad;
+};
+
 struct sympix_plan_s {
     sympix_grid_t grid = nullptr;
     int nops = 0, ring0 = 0, ring1 = 0;
@@ -144,6 +156,7 @@ struct sympix_plan_s {
     // sampling schedule (built once)
     std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
     std::vector<SampleItem> items_dense;
+    std::vector<ConvItem> items_conv;  // every block in tiles of 128 pixels
     // factorisation work lists, each most expensive first: periodic band with
     // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16, [5] 16 < w <= 64;
     // [3] dense format with n <= 1024; [4] everything else
@@ -170,6 +183,7 @@ struct sympix_plan_s {
     sympix::DevBuf<PairEntry> d_entries;
     sympix::DevBuf<SampleItem> d_items_pband[5];
     sympix::DevBuf<SampleItem> d_items_dense;
+    sympix::DevBuf<ConvItem> d_items_conv;
     sympix::DevBuf<int32_t> d_factor_items[6];
     sympix::DevBuf<int32_t> d_f32_items;
     sympix::DevBuf<F32Slice> d_f32_slices;

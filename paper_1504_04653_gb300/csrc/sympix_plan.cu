@@ -321,6 +321,12 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             for (int64_t e0 = 0; e0 < ne; e0 += 256) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
         }
     }
+    // convolution work items: every block's ring in tiles of 128 pixels
+    for (size_t b = 0; b < pl->blocks.size(); ++b) {
+        const BlockDesc &bd = pl->blocks[b];
+        for (int q0 = 0; q0 < bd.n; q0 += 128)
+            pl->items_conv.push_back({(int32_t)b, q0, grid->offset[bd.ring], grid->stride[bd.ring], 0});
+    }
     // factorisation work lists, most expensive blocks first
     std::vector<int32_t> order(pl->blocks.size());
     std::iota(order.begin(), order.end(), 0);
@@ -386,7 +392,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         (rc = pl->d_shadow.alloc(pl->factor_items[5].empty() ? 1 : std::max<int64_t>(pl->size_pband, 1))))
         return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
-        (rc = pl->d_items_dense.upload(pl->items_dense)))
+        (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_items_conv.upload(pl->items_conv)))
         return fail(rc);
     for (int bkt = 0; bkt < 5; ++bkt)
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);

@@ -68,6 +68,7 @@ SIGNATURES = [
     ("sympix_autotune", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
     ("sympix_plan_tuning", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     ("sympix_trace_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), _i32p]),
+    ("sympix_convolve", _i, [_vp, _vp, _i, _vp, _vp]),
     ("sympix_plan_free", None, [_vp]),
     ("sympix_step_create", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_vp)]),
     ("sympix_step_launch", _i, [_vp, _i, _vp]),
@@ -352,6 +353,19 @@ class Step:
 def sympix_step_create(plan: Plan, bl, dl, ninv, blocks, info, storage="pband", sample_precision="fp32",
                        factor_precision="fp32") -> Step:
     return Step(plan, bl, dl, ninv, blocks, info, storage, sample_precision, factor_precision)
+
+
+def sympix_convolve(plan: Plan, f, precision="fp64", out=None, stream=None):
+    """g = B^ f (pixel-domain convolution); f: CUDA float64 [nops, npix]."""
+    import torch
+    if f.dtype != torch.float64 or tuple(f.shape) != (plan.nops, plan.grid.npix):
+        raise SympixError(EINVAL, f"f must be float64 [{plan.nops}, {plan.grid.npix}]")
+    if out is None:
+        out = torch.zeros_like(f)
+    elif out.dtype != torch.float64 or out.numel() < f.numel():
+        raise SympixError(EINVAL, "g buffer too small")
+    _check(lib().sympix_convolve(plan.handle, _ptr(f), PRECISIONS[precision], _ptr(out), _stream(stream)))
+    return out
 
 
 # -- host-side views of the block buffer (for tests and users) -----------------------

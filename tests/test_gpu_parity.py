@@ -379,3 +379,86 @@ def test_batched_wide_operators(S, dev, precision):
             if info == 0:
                 L = S.unpack_block(r["factored"], plan, "pband", o, j, factored=True)
                 assert _err(L @ L.T, ref) <= 10 * tol, (o, j, _err(L @ L.T, ref))
+
+
+# -- pixel-domain convolution g = B^ f (Eq. convolution-pixel) --------------------
+
+def _pixel_ring_col(grid):
+    npix = int(grid.npix)
+    ring = np.zeros(npix, np.int32)
+    col = np.zeros(npix, np.int32)
+    for r in range(grid.nrings):
+        c = np.arange(int(grid.nring[r]))
+        idx = grid.ring_offset[r] + c * grid.ring_stride[r]
+        ring[idx] = r
+        col[idx] = c
+    return ring, col
+
+
+def _convolve(S, dev, lmax, bl_h, radii, f_h, precision, ring0=0, ring1=None):
+    import torch
+    grid = S.Grid(lmax)
+    plan = S.Plan(grid, radii, ring0, ring1)
+    bl = torch.tensor(bl_h, dtype=torch.float64, device=dev)
+    S.sympix_kernel_table(plan, bl, torch.zeros_like(bl))
+    f = torch.tensor(f_h, dtype=torch.float64, device=dev)
+    g = S.sympix_convolve(plan, f, precision=precision)
+    return grid, g.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32x2", "fp32"])
+def test_convolve_lmax64_every_pixel(S, dev, precision):
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(wl.lmax)
+    f = np.random.default_rng(21).standard_normal((1, int(grid.npix)))
+    _, g = _convolve(S, dev, wl.lmax, wl.beams(), wl.radii(), f, precision)
+    ring, col = _pixel_ring_col(grid)
+    ref, pairs = O.convolve(O.grid(wl.lmax), wl.beams()[0], wl.radii()[0], f[0], ring, col)
+    assert pairs > 0
+    assert _err(g[0], ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_convolve_lmax500_sampled(S, dev, precision):
+    wl = W.WORKLOADS["lmax500"]
+    grid = S.Grid(wl.lmax)
+    f = np.random.default_rng(22).standard_normal((1, int(grid.npix)))
+    _, g = _convolve(S, dev, wl.lmax, wl.beams(), wl.radii(), f, precision)
+    ring, col = _pixel_ring_col(grid)
+    pick = np.random.default_rng(23).choice(int(grid.npix), 300, replace=False)
+    pick = np.concatenate([pick, grid.ring_offset[[0, 1, 250, 500]]])  # poles, equator
+    ref, _ = O.convolve(O.grid(wl.lmax), wl.beams()[0], wl.radii()[0], f[0], ring[pick], col[pick])
+    assert _err(g[0][pick], ref) <= TOL[precision]
+
+
+def test_convolve_full_sky_support_and_two_operators(S, dev):
+    """r_s >= pi couples every pixel pair: each ring is visited whole, once;
+    two operators with different kernels and maps in one call."""
+    lmax = 16
+    grid = S.Grid(lmax)
+    npix = int(grid.npix)
+    l = np.arange(lmax + 1)
+    bl = np.stack([np.exp(-0.01 * l * (l + 1)), 1.0 / (1.0 + l)])
+    f = np.random.default_rng(24).standard_normal((2, npix))
+    _, g = _convolve(S, dev, lmax, bl, [math.pi, 0.9], f, "fp64")
+    ring, col = _pixel_ring_col(grid)
+    og = O.grid(lmax)
+    for o, r_s in enumerate([math.pi, 0.9]):
+        ref, pairs = O.convolve(og, bl[o], r_s, f[o], ring, col)
+        if o == 0:
+            assert pairs == npix * npix
+        assert _err(g[o], ref) <= 1e-10
+
+
+def test_convolve_ring_range(S, dev):
+    """A plan over rings [ring0, ring1) writes exactly those rings' pixels,
+    with the values of the whole-sphere plan."""
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(wl.lmax)
+    f = np.random.default_rng(25).standard_normal((1, int(grid.npix)))
+    _, full = _convolve(S, dev, wl.lmax, wl.beams(), wl.radii(), f, "fp64")
+    _, part = _convolve(S, dev, wl.lmax, wl.beams(), wl.radii(), f, "fp64", ring0=20, ring1=40)
+    ring, _ = _pixel_ring_col(grid)
+    inside = (ring >= 20) & (ring < 40)
+    assert np.array_equal(part[0][inside], full[0][inside])
+    assert np.all(part[0][~inside] == 0.0)
