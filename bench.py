@@ -167,9 +167,7 @@ ALU_PEAK = {"fp64": (FP64_NOMINAL, "nominal FP64 1.25 TFLOP/s (a DFMA probe meas
 # profiles/; an entry is removed when its kernel changes.
 TRAFFIC = {
     # profiles/dram_lmax3000_mixed_step.md: 472.2 MB read + 371.6 MB written
-    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_border_pass"): 843817472,
     ("lmax3000_fwhm5", "fp32:fp32", "k_table"): 799744,
-    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_band_pass"): 853650944,
 }
 
 
@@ -195,6 +193,8 @@ def kernel_work(plan, grid, wl, elements, sprec, fprec):
         "k_f32_band_pass": ("alu", float(sum((n - w) * (w * (w + 1) + w + 2) for n, w in f32)), "fp32"),
         "k_f32_border_pass": ("alu", float(sum((n - w) * (2 * w * w + w + w * (w + 1)) for n, w in f32)), "fp32"),
         "k_f32_out": ("hbm", (l11 + l21) * 12.0, "fp32"),
+        "k_f32_fused": ("alu", float(sum((n - w) * (w * (w + 1) + w + 2 + 2 * w * w + w + w * (w + 1))
+                                         for n, w in f32 if w <= 12)), "fp32"),
         "k_factor_band": ("alu", factor_flops(plan), fprec),
     }
 

@@ -644,6 +644,7 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
         s_cnt[threadIdx.x] = cnt;
     }
     __syncthreads();
+#pragma unroll
     for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
         const int L = i / kTileE, e = i % kTileE;
         float v = 0.0f;
@@ -653,6 +654,7 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
     __syncthreads();
     const int lim = sl.rows * RL;
     float *dst = sh + sl.sh + (int64_t)e0 * 32;
+#pragma unroll
     for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
         const int e = i >> 5, L = i & 31;
         if (e0 + e < lim) dst[e * 32 + L] = tile[e][L];
@@ -693,7 +695,8 @@ struct StaticFor<E, E> {
 // so that all take part in the staging); stage: the CTA's two period
 // buffers, laid out like the shadow.
 template <int W>
-__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor) {
+__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor,
+                                        volatile int *prog) {
     constexpr int RL = W + 1, CH = RL * RL;
     float *band = shs + lane;  // element e at band[32 e]
     auto issue = [&](int per) {
@@ -776,23 +779,35 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
             StaticFor<0, RL>::run(part);
         }
         if (bad) m = 0;  // stop this lane; the warp keeps staging
+        // every 4th period: this period's L rows reach L2 (where the border
+        // pass stages from) before the flag says rows < (p+1)(W+1) are final
+        const bool publish = prog && (p & 3) == 3;
+        if (publish) __threadfence();
         __syncwarp();    // every lane is done with the buffer the next copies overwrite
+        if (publish && lane == 0) *prog = p + 1;
     }
     cp_async_wait<0>();
+    if (prog) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) *prog = 0x7fffffff;
+    }
     return bad ? kRescue : 0;
 }
 
 template <int W>
 struct F32BandDispatch {
-    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor) {
-        if (w == W) return f32_band<W>(shs, lane, m, mmax, stage, floor);
-        return F32BandDispatch<W - 1>::run(w, shs, lane, m, mmax, stage, floor);
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+                              volatile int *prog = nullptr) {
+        if (w == W) return f32_band<W>(shs, lane, m, mmax, stage, floor, prog);
+        return F32BandDispatch<W - 1>::run(w, shs, lane, m, mmax, stage, floor, prog);
     }
 };
 template <>
 struct F32BandDispatch<0> {
-    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor) {
-        return w == 0 ? f32_band<0>(shs, lane, m, mmax, stage, floor) : -1;
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+                              volatile int *prog = nullptr) {
+        return w == 0 ? f32_band<0>(shs, lane, m, mmax, stage, floor, prog) : -1;
     }
 };
 
@@ -829,14 +844,27 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict
 // through shared memory to the corner sums S = L21 L21^T, which the 8 warps
 // share pair by pair.  At the end one thread per block factors its corner
 // A22 - S = L22 L22^T in FP64.
-template <int W, int NT>
+// FUSED: the CTA's warp 0 runs the band pass of the same slice at the same
+// time; this function's NT threads are threads 32 .. 32+NT-1, synchronise
+// among themselves on named barrier 1, stage only rows the band warp has
+// published as final (*prog = periods done), and take the blocks' band-pass
+// results from bandres at the end.
+template <int W, int NT, bool FUSED>
 __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
                                            const double *__restrict__ out, const int64_t *s_off, const int *s_n,
-                                           const int *s_live, float *stage, int *binfo) {
+                                           const int *s_live, float *stage, int *binfo, volatile int *prog,
+                                           const int *bandres) {
     constexpr int RL = W + 1, CH = RL * RL;
     constexpr int NWARP = NT / 32;
     constexpr int R = (W + NWARP - 1) / NWARP;  // border rows per lane
-    const int lane = threadIdx.x & 31, b0 = (threadIdx.x >> 5) * R;
+    const int tb = (int)threadIdx.x - (FUSED ? 32 : 0);
+    auto bsync = [] {
+        if (FUSED)
+            asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory");
+        else
+            __syncthreads();
+    };
+    const int lane = tb & 31, b0 = (tb >> 5) * R;
     const bool rows = b0 < W;       // warp-uniform: this warp owns border rows
     const int n = s_n[lane], m = n - W;
     const bool live = s_live[lane];
@@ -846,16 +874,21 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     auto issue = [&](int per) {
         const int r0 = per * RL;
         if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
+            if (FUSED) {  // wait until the band warp has finished these rows
+                int spins = 0;
+                while (*prog < per + 1 && ++spins < (1 << 22)) __nanosleep(64);
+                __threadfence_block();
+            }
             float *dst = stage + (per % 3) * CH * 32;
             const float *src = shs + (int64_t)r0 * RL * 32;
-            for (int i = threadIdx.x; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
+            for (int i = tb; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
         }
         cp_async_commit();
     };
     float *vbuf = stage + 3 * CH * 32;  // two periods of L21 values, [b][column][lane]
     float *vb = vbuf;                   // the current period's
     float *abuf = vbuf + 2 * W * RL * 32;  // A21 at the last W columns, [b][c][lane]: A[m+b][m-W+c]
-    for (int i = threadIdx.x; i < W * W * 32; i += NT) {
+    for (int i = tb; i < W * W * 32; i += NT) {
         const int L = i & 31, bc = i >> 5, bb = bc / (W > 0 ? W : 1), c = bc - bb * W;
         float v = 0.0f;
         if (s_live[L]) {
@@ -917,7 +950,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     // W (W+1)/2 pairs are dealt round-robin to the warps, lane = block;
     // each period's L21 values pass through vbuf
     constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + NWARP - 1) / NWARP;
-    const int wq = threadIdx.x >> 5;
+    const int wq = tb >> 5;
     int pb[NP > 0 ? NP : 1], pb2[NP > 0 ? NP : 1];
     float sacc[NP > 0 ? NP : 1];
 #pragma unroll
@@ -945,7 +978,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     const int PW = (kc - 1) / RL;  // the last period
     for (int p = 0; p <= PW; ++p) {
         cp_async_wait<1>();  // period p has landed
-        __syncthreads();     // ... for every thread's copies; period p-1's buffer is free
+        bsync();             // ... for every thread's copies; period p-1's buffer is free
         issue(p + 2);
         if (p > 0) accumulate(vbuf + ((p - 1) & 1) * W * RL * 32);
         vb = vbuf + (p & 1) * W * RL * 32;
@@ -967,17 +1000,18 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         }
     }
     cp_async_wait<0>();
-    __syncthreads();
+    __syncthreads();  // (fused: the band warp is done too, bandres is final)
     accumulate(vbuf + (PW & 1) * W * RL * 32);
     // the corner: sums to shared memory [block][b][b2], then one thread per
     // block factors C = A22 - S = L22 L22^T in FP64
     float *sS = stage;  // the staging is free now
-    __syncthreads();
+    bsync();
 #pragma unroll
     for (int i = 0; i < NP; ++i)
         if (wq + NWARP * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
-    __syncthreads();
-    if (threadIdx.x < 32 && live) {
+    bsync();
+    const bool live_end = FUSED ? (live && bandres[lane] == 0) : live;
+    if (tb < 32 && live_end) {
         double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
         double *outp = const_cast<double *>(out);
         const PBandView v{outp + s_off[lane], outp + s_off[lane] + (int64_t)n * RL, n, W, m};
@@ -1005,21 +1039,24 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     }
 }
 
-template <int W, int WMIN, int NT>
+template <int W, int WMIN, int NT, bool FUSED = false>
 struct F32BorderDispatch {
     __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
-                               const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo) {
+                               const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo,
+                               volatile int *prog = nullptr, const int *bandres = nullptr) {
         if (w == W) {
-            f32_border<W, NT>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
+            f32_border<W, NT, FUSED>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog, bandres);
             return;
         }
-        F32BorderDispatch<W - 1, WMIN, NT>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo);
+        F32BorderDispatch<W - 1, WMIN, NT, FUSED>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog,
+                                                       bandres);
     }
 };
-template <int WMIN, int NT>
-struct F32BorderDispatch<WMIN - 1, WMIN, NT> {
+template <int WMIN, int NT, bool FUSED>
+struct F32BorderDispatch<WMIN - 1, WMIN, NT, FUSED> {
     __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
-                               const int *, const int *, float *, int *) {}
+                               const int *, const int *, float *, int *, volatile int * = nullptr,
+                               const int * = nullptr) {}
 };
 
 // floats: three staged periods, two periods of L21 values and the last W
@@ -1035,6 +1072,7 @@ struct SliceBlocks {
 
 __device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice &sl, const int32_t *items,
                                                   const BlockDesc *blocks, const int32_t *info) {
+    // info == nullptr: every block of the slice counts as live
     if (threadIdx.x < 32) {
         const int L = threadIdx.x;
         int64_t off = 0;
@@ -1044,7 +1082,7 @@ __device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice
             const BlockDesc bd = blocks[bi];
             off = bd.off_pband;
             n = bd.n;
-            live = info[bi] == 0;
+            live = info ? info[bi] == 0 : 1;
         }
         t.off[L] = off;
         t.n[L] = n;
@@ -1069,6 +1107,51 @@ __global__ void __launch_bounds__(NT) k_f32_border_pass(const F32Slice *__restri
     load_slice_blocks(t, sl, items, blocks, info);
     F32BorderDispatch<16, 1, NT>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm, binfo);
     if (threadIdx.x < 32 && t.live[threadIdx.x] && sl.w > 0) info[t.bi[threadIdx.x]] = binfo[threadIdx.x];
+}
+
+// Band and border passes of one slice in one CTA, widths 1..kFusedWMax:
+// warp 0 eliminates the band (f32_band) and publishes after every period
+// how many periods of L11 rows are final; kFusedBorderThreads threads run
+// the border sweep (f32_border, FUSED) behind it, so the two latency-bound
+// chains overlap instead of running one after the other.  The border's waits
+// are bounded (a wait that runs out lets the sweep proceed; it cannot run
+// out unless the band warp stalls for ~0.3 s).
+constexpr int kFusedWMax = 12, kFusedBorderThreads = 256;
+constexpr int kFusedBandStage = 2 * 13 * 13 * 32;  // floats: two periods of W = 12
+// floats: band stage, then three staged periods, two periods of L21 values
+// and the last W columns of A21, W = 12
+constexpr int kFusedSmem = kFusedBandStage + 3 * 13 * 13 * 32 + 2 * 12 * 13 * 32 + 12 * 12 * 32;
+
+__global__ void __launch_bounds__(32 + kFusedBorderThreads)
+    k_f32_fused(const F32Slice *__restrict__ slices, const int32_t *__restrict__ items,
+                const BlockDesc *__restrict__ blocks, float *__restrict__ sh, float *__restrict__ l21,
+                const double *__restrict__ out, int32_t *__restrict__ info, float floor) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ SliceBlocks t;
+    __shared__ int binfo[32], bandres[32];
+    __shared__ int prog_s;
+    volatile int *prog = &prog_s;
+    const F32Slice sl = slices[blockIdx.x];
+    load_slice_blocks(t, sl, items, blocks, nullptr);
+    if (threadIdx.x == 0) *prog = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int L = threadIdx.x;
+        const int m = L < sl.count ? t.n[L] - sl.w : 0;
+        bandres[L] = F32BandDispatch<kFusedWMax>::run(sl.w, sh + sl.sh, L, m, sl.rows - sl.w, fsm, floor, prog);
+        __syncthreads();  // the border sweep's end
+    } else if (sl.w == 0) {
+        __syncthreads();
+    } else {
+        F32BorderDispatch<kFusedWMax, 1, kFusedBorderThreads, true>::run(
+            sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, fsm + kFusedBandStage, binfo, prog,
+            bandres);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && threadIdx.x < sl.count) {
+        const int L = threadIdx.x;
+        info[t.bi[L]] = (bandres[L] != 0 || sl.w == 0) ? bandres[L] : binfo[L];
+    }
 }
 
 // The factor back to the FP64 blocks: L11 rows from the band shadow and
@@ -1106,6 +1189,7 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
     const int kc = sl.rows - W;
     const int lim = part21 ? W * kc : sl.rows * RL;
     const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
+#pragma unroll
     for (int i = threadIdx.x; i < kTileE * 32; i += 256) {
         const int e = i >> 5, L = i & 31;
         tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
@@ -1503,17 +1587,30 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
             k_f32_shadow_in<<<(unsigned)pl->f32_tiles.size(), 256, 0, st>>>(
                 pl->d_f32_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks, pl->d_shadow_il.p);
             trace_mark(pl, st, "k_f32_shadow_in");
-            const size_t smem = (size_t)kF32BandStage * sizeof(float);
-            cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_f32_band_pass<<<(unsigned)ns, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p,
-                                                           pl->d_shadow_il.p, info, (float)pl->fp32_pivot_floor);
-            trace_mark(pl, st, "k_f32_band_pass");
-            const size_t bs = (size_t)kF32BorderStage * sizeof(float);
-            auto kb = pl->border_threads == 256 ? k_f32_border_pass<256> : k_f32_border_pass<512>;
-            cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
-            kb<<<(unsigned)ns, pl->border_threads, bs, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow_il.p,
-                                                            pl->d_l21_il.p, blocks, info);
-            trace_mark(pl, st, "k_f32_border_pass");
+            const int nf = pl->f32_slices_fused;  // slices with w <= kFusedWMax (they come first)
+            if (nf > 0) {
+                const size_t fs = (size_t)kFusedSmem * sizeof(float);
+                cudaFuncSetAttribute(k_f32_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+                k_f32_fused<<<(unsigned)nf, 32 + kFusedBorderThreads, fs, st>>>(
+                    sl, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow_il.p, pl->d_l21_il.p, blocks, info,
+                    (float)pl->fp32_pivot_floor);
+                trace_mark(pl, st, "k_f32_fused");
+            }
+            if (ns > nf) {
+                const size_t smem = (size_t)kF32BandStage * sizeof(float);
+                cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_f32_band_pass<<<(unsigned)(ns - nf), 32, smem, st>>>(sl + nf, pl->d_f32_items.p, pl->d_blocks.p,
+                                                                      pl->d_shadow_il.p, info,
+                                                                      (float)pl->fp32_pivot_floor);
+                trace_mark(pl, st, "k_f32_band_pass");
+                const size_t bs = (size_t)kF32BorderStage * sizeof(float);
+                auto kb = pl->border_threads == 256 ? k_f32_border_pass<256> : k_f32_border_pass<512>;
+                cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs);
+                kb<<<(unsigned)(ns - nf), pl->border_threads, bs, st>>>(sl + nf, pl->d_f32_items.p, pl->d_blocks.p,
+                                                                       pl->d_shadow_il.p, pl->d_l21_il.p, blocks,
+                                                                       info);
+                trace_mark(pl, st, "k_f32_border_pass");
+            }
             k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(
                 pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
                 pl->d_l21_il.p, blocks);

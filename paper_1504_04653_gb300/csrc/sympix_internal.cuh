@@ -168,6 +168,7 @@ struct sympix_plan_s {
     std::vector<F32Slice> f32_slices;
     std::vector<int2> f32_tiles;  // (slice, first element) of the band shadow transposes
     std::vector<int2> f32_out_tiles;  // the same, then (slice, -1 - first element) of L21
+    int f32_slices_fused = 0;     // slices with w <= 12, band and border fused (they come first)
     int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;

@@ -376,6 +376,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                     tiles21.push_back(make_int2((int)pl->f32_slices.size(), (int)(-1 - e0)));
                 sh += 32 * elems;
                 l21 += 32 * elems21;
+                if (w <= 12) ++pl->f32_slices_fused;
                 pl->f32_slices.push_back(sl);
             }
         }
@@ -581,7 +582,8 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
             // shadow in, band pass, border pass (with the corners), FP64
             // write-back, then the FP64 rescue launches (which return at
             // once for blocks that need none)
-            f = 4;
+            const int nsl = (int)pl->f32_slices.size(), nfu = pl->f32_slices_fused;
+            f = 2 + (nfu > 0 ? 1 : 0) + (nsl > nfu ? 2 : 0);
             f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
