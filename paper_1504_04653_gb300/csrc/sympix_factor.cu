@@ -1116,7 +1116,7 @@ __global__ void __launch_bounds__(NT) k_f32_border_pass(const F32Slice *__restri
 // chains overlap instead of running one after the other.  The border's waits
 // are bounded (a wait that runs out lets the sweep proceed; it cannot run
 // out unless the band warp stalls for ~0.3 s).
-constexpr int kFusedWMax = 12, kFusedBorderThreads = 256;
+constexpr int kFusedWMax = 12, kFusedBorderThreads = 320;
 constexpr int kFusedBandStage = 2 * 13 * 13 * 32;  // floats: two periods of W = 12
 // floats: band stage, then three staged periods, two periods of L21 values
 // and the last W columns of A21, W = 12
