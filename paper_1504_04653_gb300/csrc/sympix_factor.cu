@@ -20,8 +20,8 @@
 //       step (band and border in one pass).
 //   16 < w <= 64: one CTA per block, window, border columns and S in shared
 //       memory indexed mod (w+1).
-//   dense storage with n <= 1024: a warp per block, right-looking, FP64;
-//   anything else: one thread per block, FP64.
+//   dense-format blocks with n <= 1024: a warp per block, right-looking,
+//   FP64; larger ones: a CTA per block, blocked right-looking, FP64.
 //
 // FP32 rescue: an FP32 elimination whose pivot falls below a floor times the
 // original diagonal marks its block, and the block is refactored in FP64
@@ -1457,64 +1457,130 @@ __global__ void __launch_bounds__(128) k_factor_dense(int nitems, const int32_t 
     if (lane == 0) info[bi] = inf;
 }
 
-// Fallback: one thread per block, FP64 (wide bands beyond the lane groups).
-template <class View>
-__device__ int factor_band_border_serial(const View &v) {
-    const int n = v.n, w = v.w, m = v.m;
-    for (int i = 0; i < m; ++i) {
-        const int j0 = max(0, i - w);
-        for (int j = j0; j <= i; ++j) {
-            double s = v.a(i, j);
-            for (int k = max(j0, j - w); k < j; ++k) s -= v.get_l(i, k) * v.get_l(j, k);
-            if (j < i) {
-                v.put_l(i, j, s / v.get_l(j, j));
-            } else {
-                if (!(s > 0.0)) return i + 1;
-                v.put_l(i, i, sqrt(s));
-            }
-        }
-    }
-    for (int b = 0; b < w; ++b) {
-        const int i = m + b;
-        for (int j = 0; j < m; ++j) {
-            double s = v.a(i, j);
-            for (int k = max(0, j - w); k < j; ++k) s -= v.get_b(b, k) * v.get_l(j, k);
-            v.put_b(b, j, s / v.get_l(j, j));
-        }
-    }
-    for (int b = 0; b < w; ++b) {
-        const int i = m + b;
-        for (int bp = 0; bp <= b; ++bp) {
-            const int j = m + bp;
-            double s = v.a(i, j);
-            for (int k = 0; k < j; ++k) s -= v.get_b(b, k) * v.get_b(bp, k);
-            if (bp < b) {
-                v.put_b(b, j, s / v.get_b(bp, j));
-            } else {
-                if (!(s > 0.0)) return i + 1;
-                v.put_b(b, j, sqrt(s));
-            }
-        }
-    }
-    return 0;
-}
+// Dense blocks with n > 1024: one CTA of 256 threads per block, right-looking
+// blocked Cholesky in FP64 with panels of 32 columns.  Per panel: warp 0
+// factors the 32 x 32 diagonal block in shared memory; the rows below solve
+// against it (forward substitution, 64 rows at a time staged in shared
+// memory); the trailing lower triangle takes the rank-32 update in 64 x 64
+// tiles, each thread a 4 x 4 sub-tile.  The matrix stays in global memory
+// (row-major n x n at the block's offset; the lower triangle is read and
+// written).  info = first non-positive pivot row + 1, or 0.
+constexpr int kDenseNB = 32, kDenseT = 64;
 
-__global__ void k_factor_serial(int nitems, const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
-                                double *__restrict__ out, int dense_storage, int32_t *__restrict__ info) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nitems) return;
-    const int bi = items[t];
+__global__ void __launch_bounds__(256) k_factor_dense_cta(int nitems, const int32_t *__restrict__ items,
+                                                          const BlockDesc *__restrict__ blocks,
+                                                          double *__restrict__ out, int dense_storage,
+                                                          int32_t *__restrict__ info) {
+    __shared__ double sd[kDenseNB][kDenseNB + 1];
+    __shared__ double pa[kDenseT][kDenseNB + 1], pb[kDenseT][kDenseNB + 1];
+    __shared__ int s_inf;
+    if ((int)blockIdx.x >= nitems) return;
+    const int bi = items[blockIdx.x];
     const BlockDesc bd = blocks[bi];
-    int res;
-    if (dense_storage) {
-        DenseView v{out + bd.off_dense, bd.n, bd.w, bd.n - bd.w};
-        res = factor_band_border_serial(v);
-    } else {
-        double *base = out + bd.off_pband;
-        PBandView v{base, base + (int64_t)bd.n * (bd.w + 1), bd.n, bd.w, bd.n - bd.w};
-        res = factor_band_border_serial(v);
+    const int n = bd.n;
+    double *A = out + (dense_storage ? bd.off_dense : bd.off_pband);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_inf = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += kDenseNB) {
+        const int nb = min(kDenseNB, n - k0);
+        // (1) diagonal block
+        for (int e = tid; e < kDenseNB * kDenseNB; e += 256) {
+            const int r = e / kDenseNB, c = e % kDenseNB;
+            sd[r][c] = (r < nb && c <= r) ? A[(int64_t)(k0 + r) * n + k0 + c] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int k = 0; k < nb; ++k) {
+                const double dkk = sd[k][k];
+                if (!(dkk > 0.0)) {  // uniform across the warp
+                    if (lane == 0) s_inf = k0 + k + 1;
+                    break;
+                }
+                const double lkk = sqrt(dkk), rl = 1.0 / lkk;
+                __syncwarp();
+                if (lane == 0) sd[k][k] = lkk;
+                if (lane > k && lane < nb) sd[lane][k] *= rl;
+                __syncwarp();
+                for (int j = k + 1; j < nb; ++j) {
+                    const double ljk = sd[j][k];
+                    if (lane >= j && lane < nb) sd[lane][j] -= sd[lane][k] * ljk;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (s_inf) break;  // uniform: read after the barrier
+        for (int e = tid; e < nb * nb; e += 256) {
+            const int r = e / nb, c = e % nb;
+            if (c <= r) A[(int64_t)(k0 + r) * n + k0 + c] = sd[r][c];
+        }
+        const int r0 = k0 + nb;
+        // (2) panel: L[i][k0..] = A[i][k0..] L_kk^-T, 64 rows at a time
+        for (int i0 = r0; i0 < n; i0 += kDenseT) {
+            const int ni = min(kDenseT, n - i0);
+            __syncthreads();
+            for (int e = tid; e < kDenseT * kDenseNB; e += 256) {
+                const int r = e / kDenseNB, c = e % kDenseNB;
+                pa[r][c] = (r < ni && c < nb) ? A[(int64_t)(i0 + r) * n + k0 + c] : 0.0;
+            }
+            __syncthreads();
+            if (tid < ni) {
+                for (int c = 0; c < nb; ++c) {
+                    double x = pa[tid][c];
+                    for (int t = 0; t < c; ++t) x -= pa[tid][t] * sd[c][t];
+                    pa[tid][c] = x / sd[c][c];
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < kDenseT * kDenseNB; e += 256) {
+                const int r = e / kDenseNB, c = e % kDenseNB;
+                if (r < ni && c < nb) A[(int64_t)(i0 + r) * n + k0 + c] = pa[r][c];
+            }
+        }
+        // (3) trailing update of the lower triangle, 64 x 64 tiles
+        const int ty = tid / 16, tx = tid % 16;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3
+        for (int i0 = r0; i0 < n; i0 += kDenseT) {
+            for (int j0 = r0; j0 <= i0; j0 += kDenseT) {
+                __syncthreads();
+                for (int e = tid; e < kDenseT * kDenseNB; e += 256) {
+                    const int r = e / kDenseNB, c = e % kDenseNB;
+                    pa[r][c] = (i0 + r < n && c < nb) ? A[(int64_t)(i0 + r) * n + k0 + c] : 0.0;
+                    pb[r][c] = (j0 + r < n && c < nb) ? A[(int64_t)(j0 + r) * n + k0 + c] : 0.0;
+                }
+                __syncthreads();
+                double acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+                for (int c = 0; c < nb; ++c) {
+                    double xa[4], xb[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        xa[a] = pa[4 * ty + a][c];
+                        xb[a] = pb[4 * tx + a][c];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], xb[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = i0 + 4 * ty + a;
+                    if (i >= n) continue;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = j0 + 4 * tx + b;
+                        if (j <= i) A[(int64_t)i * n + j] -= acc[a][b];
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
-    info[bi] = res;
+    if (tid == 0) info[bi] = s_inf;
 }
 
 }  // namespace sympix
@@ -1655,9 +1721,9 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
                                                                         blocks, dense ? 1 : 0, info);
     if (nd) trace_mark(pl, st, "k_factor_dense");
     if (ns)
-        k_factor_serial<<<(unsigned)((ns + 31) / 32), 32, 0, st>>>(ns, pl->d_factor_items[4].p, pl->d_blocks.p, blocks,
-                                                                  dense ? 1 : 0, info);
-    if (ns) trace_mark(pl, st, "k_factor_serial");
+        k_factor_dense_cta<<<(unsigned)ns, 256, 0, st>>>(ns, pl->d_factor_items[4].p, pl->d_blocks.p, blocks,
+                                                         dense ? 1 : 0, info);
+    if (ns) trace_mark(pl, st, "k_factor_dense_cta");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_factor_blocks: launch");
     return SYMPIX_OK;

@@ -462,3 +462,52 @@ def test_convolve_ring_range(S, dev):
     inside = (ring >= 20) & (ring < 40)
     assert np.array_equal(part[0][inside], full[0][inside])
     assert np.all(part[0][~inside] == 0.0)
+
+
+# -- large dense-format blocks (a CTA per block, blocked Cholesky) ----------------
+
+def _dense_block(sampled, plan, storage, ring):
+    off, n, w, fmt = plan.block_layout(storage, 0, ring)
+    return np.array(sampled[off:off + n * n]).reshape(n, n), fmt, n
+
+
+def test_dense_storage_large_blocks_lmax1500(S, dev):
+    """Dense storage at l_max = 1500 (rings of ~3000 pixels): L L^T
+    reproduces the sampled block to FP64 accuracy."""
+    wl = W.WORKLOADS["lmax1500"]
+    grid = S.Grid(wl.lmax)
+    j0 = grid.nrings // 2 - 1
+    r = _run(S, dev, wl, grid=grid, ring0=j0, ring1=j0 + 2, precision="fp64", storage="dense", factor=True)
+    assert np.all(r["info"] == 0)
+    for j in (j0, j0 + 1):
+        M, _, n = _dense_block(r["sampled"], r["plan"], "dense", j)
+        L = np.tril(_dense_block(r["factored"], r["plan"], "dense", j)[0])
+        assert n > 1024
+        assert _err(L @ L.T, np.tril(M) + np.tril(M, -1).T) <= 1e-11
+
+
+def test_pband_storage_dense_format_large_blocks(S, dev):
+    """A beam wide enough that the equatorial blocks are stored dense in
+    periodic-band storage (w > 64) with n > 1024; FP64 factor."""
+    wl = W.Workload("wide600", 600, [240.0], [0.0], [31])
+    grid = S.Grid(wl.lmax)
+    j0 = grid.nrings // 2 - 1
+    r = _run(S, dev, wl, grid=grid, ring0=j0, ring1=j0 + 2, precision="fp64", storage="pband", factor=True,
+             factor_precision="fp64")
+    for j in (j0, j0 + 1):
+        M, fmt, n = _dense_block(r["sampled"], r["plan"], "pband", j)
+        assert fmt == S.BLOCK_DENSE and n > 1024
+    if np.all(r["info"] == 0):
+        for j in (j0, j0 + 1):
+            M, _, _ = _dense_block(r["sampled"], r["plan"], "pband", j)
+            L = np.tril(_dense_block(r["factored"], r["plan"], "pband", j)[0])
+            assert _err(L @ L.T, M) <= 1e-11
+    else:  # an indefinite block: the same verdict as numpy's dense Cholesky
+        for k, j in enumerate((j0, j0 + 1)):
+            M, _, _ = _dense_block(r["sampled"], r["plan"], "pband", j)
+            try:
+                np.linalg.cholesky(M)
+                ok = True
+            except np.linalg.LinAlgError:
+                ok = False
+            assert ok == (r["info"][k] == 0)
