@@ -27,6 +27,9 @@ int cuda_error(cudaError_t e, const char *what);
 // capturing); `name` labels the span since the previous mark, null starts a call.
 void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
 
+// Elements of a dense-format block sampled by one CTA (a warp each).
+constexpr int kDenseItemElems = 8;
+
 // Elements per block in one CTA of the FP32 shadow transposes (x 32 blocks).
 constexpr int kTileE = 128;
 

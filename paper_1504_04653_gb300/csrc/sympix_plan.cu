@@ -310,7 +310,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     pl->size_dense = offd;
 
     // sampling work items: pband blocks in tiles of 128 columns, bucketed by
-    // band width; dense blocks in tiles of 256 elements
+    // band width; dense blocks in tiles of 8 elements (a warp each)
     for (size_t b = 0; b < pl->blocks.size(); ++b) {
         const BlockDesc &bd = pl->blocks[b];
         if (bd.format == SYMPIX_BLOCK_PBAND) {
@@ -318,7 +318,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             for (int q0 = 0; q0 < bd.n; q0 += 128) pl->items_pband[bucket].push_back({(int32_t)b, q0});
         } else {
             const int64_t ne = (int64_t)bd.n * bd.n;
-            for (int64_t e0 = 0; e0 < ne; e0 += 256) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
+            for (int64_t e0 = 0; e0 < ne; e0 += kDenseItemElems) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
         }
     }
     // convolution work items: every block's ring in tiles of 128 pixels

@@ -35,19 +35,23 @@ __global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, flo
 }
 
 // Small or wrapping blocks (every pixel pair of the ring may couple): one
-// thread per element (q, r), every pixel of every coupled ring tested, the
-// separation index reduced to |dphi| <= pi.  FP64.
-__global__ void __launch_bounds__(256) k_sample_dense(const SampleItem *__restrict__ items,
-                                                      const BlockDesc *__restrict__ blocks,
-                                                      const PairEntry *__restrict__ entries, int64_t nslots,
-                                                      int64_t npix, const double *__restrict__ tb,
-                                                      const double *__restrict__ td, const double *__restrict__ ninv,
-                                                      double *__restrict__ out, int dense_storage) {
+// warp per element (q, r), its lanes sharing the pixels of every coupled
+// ring, the separation index reduced to |dphi| <= pi; the partial sums meet
+// in a fixed-order shuffle tree.  FP64.
+
+__global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const SampleItem *__restrict__ items,
+                                                                   const BlockDesc *__restrict__ blocks,
+                                                                   const PairEntry *__restrict__ entries,
+                                                                   int64_t nslots, int64_t npix,
+                                                                   const double *__restrict__ tb,
+                                                                   const double *__restrict__ td,
+                                                                   const double *__restrict__ ninv,
+                                                                   double *__restrict__ out, int dense_storage) {
     const SampleItem it = items[blockIdx.x];
     const BlockDesc bd = blocks[it.block];
-    const int n = bd.n;
-    const int64_t eidx = (int64_t)it.q0 + threadIdx.x;
-    if (eidx >= (int64_t)n * n) return;
+    const int n = bd.n, lane = threadIdx.x & 31;
+    const int64_t eidx = (int64_t)it.q0 + (threadIdx.x >> 5);
+    if (eidx >= (int64_t)n * n) return;  // uniform per warp
     const int q = (int)(eidx / n), r = (int)(eidx % n);
     const int64_t tbase = (int64_t)bd.op * nslots;
     const double *nv = ninv + (int64_t)bd.op * npix;
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(256) k_sample_dense(const SampleItem *__restri
         const int64_t half = P * pe.nrho;  // P Q g
         const int64_t T2 = 2 * half;
         const double *trow = tb + tbase + pe.tab;
-        for (int p = 0; p < pe.nrho; ++p) {
+        for (int p = lane; p < pe.nrho; p += 32) {
             int64_t zq = ((2 * q + 1) * Q - (2 * (int64_t)p + 1) * P) % T2;
             if (zq > half) zq -= T2;
             if (zq <= -half) zq += T2;
@@ -72,10 +76,14 @@ __global__ void __launch_bounds__(256) k_sample_dense(const SampleItem *__restri
             acc = fma(bq * nv[pe.noff + (int64_t)p * pe.nstride], br, acc);
         }
     }
-    int k = q > r ? q - r : r - q;
-    if (n - k < k) k = n - k;
-    if (k < bd.dK) acc += td[tbase + bd.dtab + k];
-    out[(dense_storage ? bd.off_dense : bd.off_pband) + (int64_t)q * n + r] = acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        int k = q > r ? q - r : r - q;
+        if (n - k < k) k = n - k;
+        if (k < bd.dK) acc += td[tbase + bd.dtab + k];
+        out[(dense_storage ? bd.off_dense : bd.off_pband) + (int64_t)q * n + r] = acc;
+    }
 }
 
 }  // namespace sympix
@@ -109,7 +117,7 @@ extern "C" int sympix_sample_blocks(sympix_plan_t pl, const double *ninv, int pr
     }
     trace_mark(pl, st, "k_sample_pband");
     if (!pl->items_dense.empty())
-        k_sample_dense<<<(unsigned)pl->items_dense.size(), 256, 0, st>>>(
+        k_sample_dense<<<(unsigned)pl->items_dense.size(), 32 * kDenseItemElems, 0, st>>>(
             pl->d_items_dense.p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, pl->grid->npix, pl->d_tab_b.p,
             pl->d_tab_d.p, ninv, blocks, dense ? 1 : 0);
     trace_mark(pl, st, "k_sample_dense");
