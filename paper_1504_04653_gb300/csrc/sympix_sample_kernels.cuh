@@ -228,6 +228,150 @@ __global__ void __launch_bounds__(128) k_sample_pband(const SampleItem *__restri
     }
 }
 
+// -- FP32, two columns per thread on the packed FP32 pipe -------------------
+// fma.rn.f32x2 / mul.rn.f32x2 apply the FP32 operation to both halves of a
+// register pair with the same rounding as the scalar instruction, so the two
+// columns q, q+1 of a thread come out exactly as the one-column kernel's.
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+    unsigned long long ua = *reinterpret_cast<unsigned long long *>(&a), ub = *reinterpret_cast<unsigned long long *>(&b),
+                       ud;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(ud) : "l"(ua), "l"(ub));
+    return *reinterpret_cast<float2 *>(&ud);
+}
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+    unsigned long long ua = *reinterpret_cast<unsigned long long *>(&a), ub = *reinterpret_cast<unsigned long long *>(&b),
+                       uc = *reinterpret_cast<unsigned long long *>(&c), ud;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(ud) : "l"(ua), "l"(ub), "l"(uc));
+    return *reinterpret_cast<float2 *>(&ud);
+}
+
+// Same-count neighbour ring for columns q and q+1: one window of 2K map
+// values serves both (column q+1's window is column q's shifted by one).
+template <int WMAX, int K>
+__device__ __forceinline__ void same_count2(float2 (&acc)[WMAX + 1], int q, int n, int w,
+                                            const float *__restrict__ n32, int nstride, const float *__restrict__ t32) {
+    float t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = t32[k];
+    float v[2 * K];
+    const int p0 = q - (K - 1);
+    if (nstride == 1 && p0 >= 0 && p0 + 2 * K - 1 < n) {
+#pragma unroll
+        for (int j = 0; j < 2 * K; ++j) v[j] = n32[p0 + j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 2 * K; ++j) {
+            int p = p0 + j;
+            p += p < 0 ? n : 0;
+            p -= p >= n ? n : 0;
+            v[j] = n32[(int64_t)p * nstride];
+        }
+    }
+    float2 wv[2 * K - 1];
+#pragma unroll
+    for (int i = 0; i < 2 * K - 1; ++i) {
+        const int sv = i - (K - 1);
+        const float ts = t[sv < 0 ? -sv : sv];
+        wv[i] = f2mul(make_float2(v[i], v[i + 1]), make_float2(ts, ts));
+    }
+#pragma unroll
+    for (int d = 0; d <= 2 * K - 2; ++d) {
+        if (d > w) break;  // offsets past the stored band (uniform per block)
+#pragma unroll
+        for (int i = 0; i < 2 * K - 1; ++i) {
+            const int a = i - (K - 1) + d;
+            if (a >= -(K - 1) && a <= K - 1) {
+                const float ta = t[a < 0 ? -a : a];
+                acc[d] = f2fma(wv[i], make_float2(ta, ta), acc[d]);
+            }
+        }
+    }
+}
+
+template <int WMAX, int K>
+struct SameCount2 {
+    __device__ static bool run(int Kr, float2 (&acc)[WMAX + 1], int q, int n, int w, const float *n32, int nstride,
+                               const float *t32) {
+        if (Kr == K) {
+            same_count2<WMAX, K>(acc, q, n, w, n32, nstride, t32);
+            return true;
+        }
+        return SameCount2<WMAX, K - 1>::run(Kr, acc, q, n, w, n32, nstride, t32);
+    }
+};
+template <int WMAX>
+struct SameCount2<WMAX, 0> {
+    __device__ static bool run(int, float2 (&)[WMAX + 1], int, int, int, const float *, int, const float *) {
+        return false;
+    }
+};
+
+// FP32 periodic-band sampling, 64 threads per 128-column tile, columns
+// q0 + 2t and q0 + 2t + 1 in thread t; output staged and written as the
+// tile's contiguous band slice.
+template <int WMAX>
+__global__ void __launch_bounds__(64) k_sample_pband_f32x2(const SampleItem *__restrict__ items,
+                                                           const BlockDesc *__restrict__ blocks,
+                                                           const PairEntry *__restrict__ entries, int64_t nslots,
+                                                           int64_t npix, const float *__restrict__ tb32,
+                                                           const float *__restrict__ td32,
+                                                           const float *__restrict__ ninv32,
+                                                           double *__restrict__ out) {
+    constexpr int KTOP = (WMAX / 2 + 1) < 17 ? (WMAX / 2 + 1) : 17;
+    __shared__ double stage[128 * (WMAX + 1)];
+    const SampleItem it = items[blockIdx.x];
+    const BlockDesc bd = blocks[it.block];
+    const int n = bd.n, w = bd.w;
+    const int q = it.q0 + 2 * (int)threadIdx.x;
+    const bool live0 = q < n, live1 = q + 1 < n;
+    float2 acc[WMAX + 1];
+#pragma unroll
+    for (int d = 0; d <= WMAX; ++d) acc[d] = make_float2(0.0f, 0.0f);
+    const int64_t tbase = (int64_t)bd.op * nslots;
+    const float *n32 = ninv32 + (int64_t)bd.op * npix;
+    if (live0) {
+        for (int e = 0; e < bd.npairs; ++e) {
+            const PairEntry pe = entries[bd.pair0 + e];
+            const int64_t tab = tbase + pe.tab;
+            bool done = false;
+            if (pe.P == 1 && pe.Q == 1)
+                done = SameCount2<WMAX, KTOP>::run(pe.mmax / 2 + 1, acc, q, n, w, n32 + pe.noff, pe.nstride, tb32 + tab);
+            if (!done) {  // any other ring pair: each column on its own
+                float a0[WMAX + 1], a1[WMAX + 1];
+#pragma unroll
+                for (int d = 0; d <= WMAX; ++d) {
+                    a0[d] = acc[d].x;
+                    a1[d] = acc[d].y;
+                }
+                general_entry<Arith<1>, WMAX>(a0, q, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr, tab);
+                if (live1) general_entry<Arith<1>, WMAX>(a1, q + 1, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr, tab);
+#pragma unroll
+                for (int d = 0; d <= WMAX; ++d) acc[d] = make_float2(a0[d], a1[d]);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d <= WMAX; ++d)
+            if (d < bd.dK) {
+                const float dv = td32[tbase + bd.dtab + d];
+                acc[d].x += dv;
+                acc[d].y += dv;
+            }
+    }
+    const int t2 = 2 * (int)threadIdx.x;
+#pragma unroll
+    for (int d = 0; d <= WMAX; ++d) {
+        if (d <= w) {
+            if (live0) stage[t2 * (w + 1) + d] = f32_to_f64_bits(acc[d].x);
+            if (live1) stage[(t2 + 1) * (w + 1) + d] = f32_to_f64_bits(acc[d].y);
+        }
+    }
+    __syncthreads();
+    const int nq = min(128, n - it.q0);
+    const int tot = nq * (w + 1);
+    double *dst = out + bd.off_pband + (int64_t)it.q0 * (w + 1);
+    for (int i = threadIdx.x; i < tot; i += 64) dst[i] = stage[i];
+}
+
 template <int PREC, bool DENSE_OUT>
 void launch_pband(sympix_plan_t pl, const double *ninv, double *blocks, cudaStream_t st) {
     const int64_t npix = pl->grid->npix;
@@ -238,6 +382,12 @@ void launch_pband(sympix_plan_t pl, const double *ninv, double *blocks, cudaStre
 #define SPX_ARGS                                                                                            \
     pl->d_items_pband[b].p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, npix, pl->d_tab_b.p, pl->d_tab_b32.p, \
         pl->d_tab_blo.p, pl->d_tab_d.p, pl->d_tab_d32.p, pl->d_tab_dlo.p, ninv, pl->d_ninv32.p, pl->d_ninvlo.p, blocks
+        if (PREC == 1 && !DENSE_OUT && wm[b] == 8) {  // two columns per thread, packed FP32 (faster here;
+                                                       // the one-column kernel is faster for wider bands)
+            k_sample_pband_f32x2<8><<<(unsigned)ni, 64, 0, st>>>(pl->d_items_pband[b].p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, npix,
+                                            pl->d_tab_b32.p, pl->d_tab_d32.p, pl->d_ninv32.p, blocks);
+            continue;
+        }
         switch (wm[b]) {
             case 8: k_sample_pband<PREC, 8, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
             case 16: k_sample_pband<PREC, 16, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
