@@ -1,0 +1,154 @@
+// FP32 factor of periodic-band blocks on the lane-interleaved shadow: the
+// transposes in and out, the separate band and border passes (widths above
+// the fused kernel's), and the launcher of the whole FP32 path.
+#include "sympix_factor_kernels.cuh"
+
+namespace sympix {
+
+// One CTA per kTileE elements x 32 blocks of a slice.
+__global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ tiles,
+                                                       const F32Slice *__restrict__ slices,
+                                                       const int32_t *__restrict__ items,
+                                                       const BlockDesc *__restrict__ blocks,
+                                                       const double *__restrict__ out, float *__restrict__ sh) {
+    __shared__ float tile[kTileE][33];
+    __shared__ int64_t s_off[32];
+    __shared__ int s_cnt[32];
+    const int2 tl = tiles[blockIdx.x];
+    const F32Slice sl = slices[tl.x];
+    const int RL = sl.w + 1, e0 = tl.y;
+    if (threadIdx.x < 32) {
+        int64_t off = 0;
+        int cnt = 0;
+        if ((int)threadIdx.x < sl.count) {
+            const BlockDesc bd = blocks[items[sl.first + threadIdx.x]];
+            off = bd.off_pband;
+            cnt = bd.n * RL;
+        }
+        s_off[threadIdx.x] = off;
+        s_cnt[threadIdx.x] = cnt;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
+        const int L = i / kTileE, e = i % kTileE;
+        float v = 0.0f;
+        if (e0 + e < s_cnt[L]) v = f64_to_f32_bits(out[s_off[L] + e0 + e]);
+        tile[e][L] = v;
+    }
+    __syncthreads();
+    const int lim = sl.rows * RL;
+    float *dst = sh + sl.sh + (int64_t)e0 * 32;
+#pragma unroll
+    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
+        const int e = i >> 5, L = i & 31;
+        if (e0 + e < lim) dst[e * 32 + L] = tile[e][L];
+    }
+}
+
+// One warp per slice, one lane per block.
+__global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict__ slices,
+                                                      const int32_t *__restrict__ items,
+                                                      const BlockDesc *__restrict__ blocks, float *__restrict__ sh,
+                                                      int32_t *__restrict__ info, float floor) {
+    extern __shared__ __align__(16) float fsm[];
+    const F32Slice sl = slices[blockIdx.x];
+    const int lane = threadIdx.x;
+    int m = 0, bi = -1;
+    if (lane < sl.count) {
+        bi = items[sl.first + lane];
+        m = blocks[bi].n - sl.w;
+    }
+    const int r = F32BandDispatch<16>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, fsm, floor);
+    if (bi >= 0) info[bi] = r;
+}
+
+// The factor back to the FP64 blocks: L11 rows from the band shadow and
+// L21 rows from the border buffer, 64 elements x 32 blocks per CTA, through
+// a shared-memory transpose (coalesced on both sides).  Blocks sent to the
+// FP64 rescue are skipped.
+__global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles, const F32Slice *__restrict__ slices,
+                                                 const int32_t *__restrict__ items,
+                                                 const BlockDesc *__restrict__ blocks,
+                                                 const int32_t *__restrict__ info, const float *__restrict__ sh,
+                                                 const float *__restrict__ l21, double *__restrict__ out) {
+    __shared__ float tile[kTileE][33];
+    __shared__ int64_t s_off[32];
+    __shared__ int s_n[32], s_live[32];
+    const int2 tl = tiles[blockIdx.x];
+    const F32Slice sl = slices[tl.x];
+    const int W = sl.w, RL = W + 1;
+    const bool part21 = tl.y < 0;
+    const int e0 = part21 ? -1 - tl.y : tl.y;
+    if (threadIdx.x < 32) {
+        const int L = threadIdx.x;
+        int64_t off = 0;
+        int n = 0, live = 0;
+        if (L < sl.count) {
+            const int bi = items[sl.first + L];
+            const BlockDesc bd = blocks[bi];
+            off = bd.off_pband;
+            n = bd.n;
+            live = info[bi] != kRescue;
+        }
+        s_off[L] = off;
+        s_n[L] = n;
+        s_live[L] = live;
+    }
+    const int kc = sl.rows - W;
+    const int lim = part21 ? W * kc : sl.rows * RL;
+    const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
+#pragma unroll
+    for (int i = threadIdx.x; i < kTileE * 32; i += 256) {
+        const int e = i >> 5, L = i & 31;
+        tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
+    }
+    __syncthreads();
+    // every element of this thread has the same e (its lanes differ): the
+    // element's (row, offset) or (border row, column) is formed once
+    const int e = threadIdx.x % kTileE, ee = e0 + e;
+    if (ee >= lim) return;
+    const int q = part21 ? ee / kc : ee / RL;          // border row b, or band row
+    const int r = part21 ? ee - q * kc : ee - q * RL;  // column k, or offset d
+#pragma unroll
+    for (int L = threadIdx.x / kTileE; L < 32; L += 256 / kTileE) {
+        const int n = s_n[L], m = n - W;
+        const bool ok = s_live[L] && (part21 ? r < m : (q < m && r <= q));
+        if (ok) {
+            const int64_t dst = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q * n + r : s_off[L] + ee;
+            out[dst] = f32_to_f64_bits(tile[e][L]);
+        }
+    }
+}
+
+void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    const int ns = (int)pl->f32_slices.size();
+    if (!ns) return;
+    const F32Slice *sl = pl->d_f32_slices.p;
+    k_f32_shadow_in<<<(unsigned)pl->f32_tiles.size(), 256, 0, st>>>(pl->d_f32_tiles.p, sl, pl->d_f32_items.p,
+                                                                   pl->d_blocks.p, blocks, pl->d_shadow_il.p);
+    trace_mark(pl, st, "k_f32_shadow_in");
+    const int nf = pl->f32_slices_fused;  // slices fused band + border (they come first)
+    if (nf > 0) launch_f32_fused(pl, nf, blocks, info, st);
+    if (ns > nf) {
+        const size_t smem = (size_t)kF32BandStage * sizeof(float);
+        cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_f32_band_pass<<<(unsigned)(ns - nf), 32, smem, st>>>(sl + nf, pl->d_f32_items.p, pl->d_blocks.p,
+                                                              pl->d_shadow_il.p, info, (float)pl->fp32_pivot_floor);
+        trace_mark(pl, st, "k_f32_band_pass");
+        if (pl->border_threads == 256)
+            launch_f32_border<256>(pl, nf, ns - nf, blocks, info, st);
+        else
+            launch_f32_border<512>(pl, nf, ns - nf, blocks, info, st);
+        trace_mark(pl, st, "k_f32_border_pass");
+    }
+    k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p,
+                                                                 pl->d_blocks.p, info, pl->d_shadow_il.p,
+                                                                 pl->d_l21_il.p, blocks);
+    trace_mark(pl, st, "k_f32_out");
+    // near-degenerate blocks: FP64 from the untouched FP64 input
+    launch_band<ArF64>(pl, false, blocks, info, st, 1);
+    trace_mark(pl, st, "k_factor_rescue");
+}
+
+}  // namespace sympix

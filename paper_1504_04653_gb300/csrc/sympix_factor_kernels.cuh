@@ -1,0 +1,573 @@
+// Shared pieces of the Cholesky factorisation kernels (sympix_factor*.cu):
+// block views, staging helpers, and the templated FP32 band / border
+// passes that both the separate and the fused FP32 kernels run.
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "sympix_arith.cuh"
+#include "sympix_internal.cuh"
+
+namespace sympix {
+
+// Element access of one block in its storage.
+struct PBandView {
+    double *band;  // n x (w+1)
+    double *bord;  // w x n
+    int n, w, m;
+    // original A[i][j], i >= j
+    __device__ double a(int i, int j) const {
+        const int d = i - j;
+        if (d <= w) return band[(int64_t)i * (w + 1) + d];
+        const int dw = j - i + n;  // wrapped: A[j][(j - dw) mod n]
+        if (dw <= w) return band[(int64_t)j * (w + 1) + dw];
+        return 0.0;
+    }
+    __device__ void put_l(int i, int j, double x) const { band[(int64_t)i * (w + 1) + (i - j)] = x; }
+    __device__ double get_l(int i, int j) const { return band[(int64_t)i * (w + 1) + (i - j)]; }
+    __device__ void put_b(int b, int j, double x) const { bord[(int64_t)b * n + j] = x; }
+    __device__ double get_b(int b, int j) const { return bord[(int64_t)b * n + j]; }
+    // A[rr][rr - w + c], c = 0..w (a band row, rr >= w)
+    __device__ const double *row_elem(int rr, int c) const { return band + (int64_t)rr * (w + 1) + (w - c); }
+};
+
+struct DenseView {
+    double *p;
+    int n, w, m;
+    __device__ double a(int i, int j) const { return p[(int64_t)i * n + j]; }
+    __device__ void put_l(int i, int j, double x) const { p[(int64_t)i * n + j] = x; }
+    __device__ double get_l(int i, int j) const { return p[(int64_t)i * n + j]; }
+    __device__ void put_b(int b, int j, double x) const { p[(int64_t)(m + b) * n + j] = x; }
+    __device__ double get_b(int b, int j) const { return p[(int64_t)(m + b) * n + j]; }
+    __device__ const double *row_elem(int rr, int c) const { return p + (int64_t)rr * n + (rr - w + c); }
+};
+
+template <bool DENSE>
+struct ViewOf;
+template <>
+struct ViewOf<false> {
+    typedef PBandView T;
+    __device__ static T make(double *out, const BlockDesc &bd) {
+        double *base = out + bd.off_pband;
+        return PBandView{base, base + (int64_t)bd.n * (bd.w + 1), bd.n, bd.w, bd.n - bd.w};
+    }
+};
+template <>
+struct ViewOf<true> {
+    typedef DenseView T;
+    __device__ static T make(double *out, const BlockDesc &bd) {
+        return DenseView{out + bd.off_dense, bd.n, bd.w, bd.n - bd.w};
+    }
+};
+
+// info value of a block whose FP32 pivots shrank below the floor: it is
+// refactored in FP64 from the untouched FP64 input (kRescued marks a
+// rescued block between the FP64 band and border passes).
+constexpr int32_t kRescue = 0x40000000;
+constexpr int32_t kRescued = 0x20000000;
+
+// Asynchronous global -> shared copies (no register round trip), used to
+// prefetch band rows several elimination steps ahead.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kPrefetch = 6;  // band rows in flight ahead of the elimination
+constexpr int kRing = 8;      // ring slots per group (> kPrefetch)
+
+// ---------------------------------------------------------------------------
+// Two-pass factorisation of periodic-band blocks.
+//
+// Pass 1 (band): one lane per block factors the band part A11 = L11 L11^T.
+// The lane keeps the active (w+1) x (w+1) triangle W[r][c] (rows k..k+w,
+// columns k..k+r) in registers; per column k it forms 1/sqrt(pivot),
+// scales column k, applies the rank-1 update and shifts the window, the
+// band row entering the window having been loaded two columns ahead.
+// Pass 2 (border): one lane per border row, G2 lanes per block, runs the
+// forward substitution L21 = A21 L11^-T along the band, the band row of L11
+// broadcast by shuffles, and accumulates the corner S = A22 - L21 L21^T on
+// the fly; the w x w corner is then factored by one lane.
+// ---------------------------------------------------------------------------
+
+constexpr int kChunk = 16;  // band rows per staged chunk
+
+// ---------------------------------------------------------------------------
+// FP32 factorisation on a shadow of the band.
+//
+// Blocks of one exact width W <= 16 are factored in slices of up to 32.  A
+// slice's band rows are converted once to an FP32 copy (the shadow) laid out
+// lane-interleaved: element e (row e / (W+1), offset e % (W+1)) of the
+// slice's block L sits at 32 e + L.  With one lane per block every warp
+// access of the band pass then covers 32 consecutive floats, and the
+// border pass stages the rows of all 32 blocks with contiguous copies.
+//   1. k_f32_shadow_in   FP64 rows -> interleaved FP32 (a shared-memory
+//                        transpose, coalesced on both sides);
+//   2. k_f32_band_pass   A11 = L11 L11^T, one lane per block;
+//   3. k_f32_border_pass L21 = A21 L11^-T into an interleaved FP32 buffer,
+//                        S = L21 L21^T and the corner A22 - S = L22 L22^T;
+//   4. k_f32_out         L11 and L21 back to the FP64 blocks.
+// Kernels are specialised on W (a slice holds one width), so every window
+// index is static.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// f(integral_constant<int, I>) for I = B .. E-1, expanded at compile time.
+template <int B, int E>
+struct StaticFor {
+    template <class F>
+    __device__ __forceinline__ static void run(F &f) {
+        f(std::integral_constant<int, B>{});
+        StaticFor<B + 1, E>::run(f);
+    }
+};
+template <int E>
+struct StaticFor<E, E> {
+    template <class F>
+    __device__ __forceinline__ static void run(F &) {}
+};
+
+// Band pass of one block in one lane, exact width W.
+//
+// The active window is the lower triangle of rows k..k+W at columns k..k+r
+// (row k+r).  Row i and column j are kept in register slot i mod (W+1) and
+// j mod (W+1), and the column loop is unrolled by one period of W+1 steps,
+// so every slot index is static and moving the window costs nothing: the
+// row retiring at step k frees the slot the row k+1+W enters.  During
+// period p (steps k = p(W+1) .. p(W+1)+W) the entering rows are exactly the
+// W+1 rows of period p+1, which the warp stages into shared memory one
+// period ahead with contiguous 16-byte copies.  Inside a period the code is
+// straight-line, so the scheduler overlaps the next pivot's rsqrt with the
+// rest of the update.  Pivots are checked against the floor as they come;
+// a block that fell below it stops and is recomputed from its FP64 input.
+//
+// shs: the slice's interleaved shadow; m: this lane's A11 size (0 for an
+// idle lane); mmax: the slice's largest m (every lane runs mmax's periods,
+// so that all take part in the staging); stage: the CTA's two period
+// buffers, laid out like the shadow.
+template <int W>
+__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor,
+                                        volatile int *prog) {
+    constexpr int RL = W + 1, CH = RL * RL;
+    float *band = shs + lane;  // element e at band[32 e]
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < mmax) {  // rows r0 .. r0 + W < the slice's rows
+            float *dst = stage + (per & 1) * CH * 32;
+            const float *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = lane; i < CH * 8; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
+        }
+        cp_async_commit();
+    };
+    issue(1);
+    float Wn[RL][RL];  // [row slot][column slot]
+    float od[RL];      // original diagonal per row slot
+#pragma unroll
+    for (int r = 0; r <= W; ++r) {
+#pragma unroll
+        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[((int64_t)r * RL + (r - c)) * 32] : 0.0f;
+        od[r] = Wn[r][r];
+    }
+    // One elimination step at phase PH (k = p RL + PH).  lrow = band row
+    // p RL; src = this lane's staged rows of period p + 1.  Rows >= m only
+    // ever feed rows >= m, which nothing reads, so they need no masking.
+    // The pivot d of row k and rs = 1/sqrt(d) arrive from the previous
+    // step: each step forms the next pivot first (one product) and starts
+    // its rsqrt before the rest of the update.
+    bool bad = !(Wn[0][0] > floor * od[0]);
+    float d = Wn[0][0], rs = rsqrtf(Wn[0][0]);
+    auto step = [&](auto PHc, float *lrow, const float *src, bool live, int kbase) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr int P1 = (PH + 1) % RL;
+        if (!live) return;
+        lrow[PH * RL * 32] = d * rs;
+        float l[RL];
+        float dn = 0.0f, rsn = 0.0f;
+        if constexpr (W >= 1) {
+            l[1] = Wn[P1][PH] * rs;
+            dn = fmaf(-l[1], l[1], Wn[P1][P1]);
+            rsn = rsqrtf(dn);
+        }
+#pragma unroll
+        for (int r = 2; r <= W; ++r) l[r] = Wn[(PH + r) % RL][PH] * rs;
+#pragma unroll
+        for (int r = 1; r <= W; ++r) lrow[((PH + r) * RL + r) * 32] = l[r];
+#pragma unroll
+        for (int r = 1; r <= W; ++r)
+#pragma unroll
+            for (int c = 1; c <= r; ++c)
+                if (r > 1 || c > 1) Wn[(PH + r) % RL][(PH + c) % RL] = fmaf(-l[r], l[c], Wn[(PH + r) % RL][(PH + c) % RL]);
+        // row k+1+W enters slot PH at columns k+1 .. k+1+W
+#pragma unroll
+        for (int c = 0; c <= W; ++c) Wn[PH][(PH + 1 + c) % RL] = src[(PH * RL + (W - c)) * 32];
+        od[PH] = Wn[PH][PH];
+        if constexpr (W >= 1) {
+            d = dn;
+            rs = rsn;
+        } else {  // a diagonal block: the next pivot is the entering row's
+            (void)dn;
+            (void)rsn;
+            d = Wn[0][0];
+            rs = rsqrtf(d);
+        }
+        // the next pivot (rows >= m are not A11's); includes d <= 0 and NaN
+        bad |= kbase + PH + 1 < m && !(d > floor * od[P1]);
+    };
+    const int PW = mmax / RL;  // the slice's last period
+    for (int p = 0; p <= PW; ++p) {
+        issue(p + 2);
+        cp_async_wait<1>();  // period p + 1 has landed
+        __syncwarp();        // ... for every lane's copies
+        const float *src = stage + ((p + 1) & 1) * CH * 32 + lane;
+        float *lrow = band + (int64_t)p * RL * RL * 32;
+        const int left = m - p * RL;  // this lane's steps left
+        const int kbase = p * RL;
+        if (left >= RL) {
+            auto full = [&](auto PHc) { step(PHc, lrow, src, true, kbase); };
+            StaticFor<0, RL>::run(full);
+        } else if (left > 0) {
+            auto part = [&](auto PHc) { step(PHc, lrow, src, decltype(PHc)::value < left, kbase); };
+            StaticFor<0, RL>::run(part);
+        }
+        if (bad) m = 0;  // stop this lane; the warp keeps staging
+        // every 4th period: this period's L rows reach L2 (where the border
+        // pass stages from) before the flag says rows < (p+1)(W+1) are final
+        const bool publish = prog && (p & 3) == 3;
+        if (publish) __threadfence();
+        __syncwarp();    // every lane is done with the buffer the next copies overwrite
+        if (publish && lane == 0) *prog = p + 1;
+    }
+    cp_async_wait<0>();
+    if (prog) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) *prog = 0x7fffffff;
+    }
+    return bad ? kRescue : 0;
+}
+
+template <int W>
+struct F32BandDispatch {
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+                              volatile int *prog = nullptr) {
+        if (w == W) return f32_band<W>(shs, lane, m, mmax, stage, floor, prog);
+        return F32BandDispatch<W - 1>::run(w, shs, lane, m, mmax, stage, floor, prog);
+    }
+};
+template <>
+struct F32BandDispatch<0> {
+    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+                              volatile int *prog = nullptr) {
+        return w == 0 ? f32_band<0>(shs, lane, m, mmax, stage, floor, prog) : -1;
+    }
+};
+
+constexpr int kF32BandStage = 2 * 17 * 17 * 32;  // floats: two periods of W = 16, 32 lanes
+
+// Border pass of one slice, exact width W: the forward substitution
+// L21 = A21 L11^-T,
+//   L21[b][k] = (A21[b][k] - sum_c L21[b][k-W+c] L11[k][k-W+c]) / L11[k][k],
+// with A21 zero except in its first W columns (the wrap) and its last W.
+// One CTA per slice; lane = block, warp q owns border rows R q .. R q + R-1
+// of all 32 blocks (R = 1 for W <= 8, 2 above).  Like the band pass it
+// walks the columns by periods of W+1 with the L11 rows staged one period
+// ahead, and keeps each row's last W values in register slot
+// (column mod W+1), so every index is static.  L21 goes to the
+// lane-interleaved FP32 border buffer (element (b, k) of block L at
+// 32 (b kc + k) + L, kc = the slice's largest m) and, a period at a time,
+// through shared memory to the corner sums S = L21 L21^T, which the 8 warps
+// share pair by pair.  At the end one thread per block factors its corner
+// A22 - S = L22 L22^T in FP64.
+// FUSED: the CTA's warp 0 runs the band pass of the same slice at the same
+// time; this function's NT threads are threads 32 .. 32+NT-1, synchronise
+// among themselves on named barrier 1, stage only rows the band warp has
+// published as final (*prog = periods done), and take the blocks' band-pass
+// results from bandres at the end.
+template <int W, int NT, bool FUSED>
+__device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
+                                           const double *__restrict__ out, const int64_t *s_off, const int *s_n,
+                                           const int *s_live, float *stage, int *binfo, volatile int *prog,
+                                           const int *bandres) {
+    constexpr int RL = W + 1, CH = RL * RL;
+    constexpr int NWARP = NT / 32;
+    constexpr int R = (W + NWARP - 1) / NWARP;  // border rows per lane
+    const int tb = (int)threadIdx.x - (FUSED ? 32 : 0);
+    auto bsync = [] {
+        if (FUSED)
+            asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory");
+        else
+            __syncthreads();
+    };
+    const int lane = tb & 31, b0 = (tb >> 5) * R;
+    const bool rows = b0 < W;       // warp-uniform: this warp owns border rows
+    const int n = s_n[lane], m = n - W;
+    const bool live = s_live[lane];
+    const PBandView view{const_cast<double *>(out) + s_off[lane],
+                         const_cast<double *>(out) + s_off[lane] + (int64_t)n * RL, n, W, m};
+    const int kc = sl.rows - W;
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
+            if (FUSED) {  // wait until the band warp has finished these rows
+                int spins = 0;
+                while (*prog < per + 1 && ++spins < (1 << 22)) __nanosleep(64);
+                __threadfence_block();
+            }
+            float *dst = stage + (per % 3) * CH * 32;
+            const float *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = tb; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
+        }
+        cp_async_commit();
+    };
+    float *vbuf = stage + 3 * CH * 32;  // two periods of L21 values, [b][column][lane]
+    float *vb = vbuf;                   // the current period's
+    float *abuf = vbuf + 2 * W * RL * 32;  // A21 at the last W columns, [b][c][lane]: A[m+b][m-W+c]
+    for (int i = tb; i < W * W * 32; i += NT) {
+        const int L = i & 31, bc = i >> 5, bb = bc / (W > 0 ? W : 1), c = bc - bb * W;
+        float v = 0.0f;
+        if (s_live[L]) {
+            const int nL = s_n[L], mL = nL - W;
+            double *o = const_cast<double *>(out) + s_off[L];
+            const PBandView vL{o, o + (int64_t)nL * RL, nL, W, mL};
+            v = f64_to_f32_bits(vL.a(mL + bb, mL - W + c));
+        }
+        abuf[i] = v;
+    }
+    float aw[R][W];  // A21 of my rows at columns < W (the wrap part)
+    float y[R][RL];  // L21 of my rows at the last W columns, slot = column mod RL
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+            aw[r][c] = (rows && live && b0 + r < W) ? f64_to_f32_bits(view.a(m + b0 + r, c)) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < RL; ++c) y[r][c] = 0.0f;
+    }
+    // column k = p RL + PH; src = this lane's staged rows of period p
+    // TAIL: some block of the warp reaches its last W columns (A21's band
+    // part) or its end in this period; otherwise no select is needed
+    auto column = [&](auto PHc, auto FIRSTc, auto TAILc, const float *src, int kbase) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr bool FIRST = decltype(FIRSTc)::value;  // p == 0: mask the columns left of 0
+        constexpr bool TAIL = decltype(TAILc)::value;
+        const int k = kbase + PH;
+        const float *row = src + PH * RL * 32;  // L11 row k: offset d at row[32 d]
+        float lr[RL];
+#pragma unroll
+        for (int d = 0; d < RL; ++d) lr[d] = row[d * 32];
+        const float rd = rsqrtf(lr[0]);
+        const float rcp = rd * rd;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int b = b0 + r;
+            float acc = 0.0f;
+            if constexpr (FIRST && PH < W) acc = aw[r][PH < W ? PH : 0];
+            if constexpr (TAIL) {  // the last W columns, without a branch
+                const int c = k - (m - W);
+                const float a = abuf[((b < W ? b : W - 1) * W + min(max(c, 0), W - 1)) * 32 + lane];
+                acc = (c >= 0 && c < W) ? a : acc;
+            }
+#pragma unroll
+            for (int cc = 0; cc < W; ++cc) {
+                if (FIRST && PH - W + cc < 0) continue;  // left of column 0
+                acc = fmaf(-y[r][(PH - W + cc + RL) % RL], lr[W - cc], acc);
+            }
+            const float val = (!TAIL || (live && b < W && k < m)) ? acc * rcp : 0.0f;
+            y[r][PH] = val;
+            if (b < W) {
+                vb[(b * RL + PH) * 32 + lane] = val;
+                if (!TAIL || k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
+            }
+        }
+    };
+    // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b: the
+    // W (W+1)/2 pairs are dealt round-robin to the warps, lane = block;
+    // each period's L21 values pass through vbuf
+    constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + NWARP - 1) / NWARP;
+    const int wq = tb >> 5;
+    int pb[NP > 0 ? NP : 1], pb2[NP > 0 ? NP : 1];
+    float sacc[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        int j = wq + NWARP * i, bb = 0;
+        while (j > bb) {  // pair j = bb (bb+1)/2 + b2
+            j -= bb + 1;
+            ++bb;
+        }
+        pb[i] = bb < W ? bb : 0;
+        pb2[i] = bb < W ? j : 0;
+        sacc[i] = 0.0f;
+    }
+    auto accumulate = [&](const float *v) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            if (wq + NWARP * i >= NPAIR) break;
+            const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+        }
+    };
+    issue(0);
+    issue(1);
+    const int PW = (kc - 1) / RL;  // the last period
+    for (int p = 0; p <= PW; ++p) {
+        cp_async_wait<1>();  // period p has landed
+        bsync();             // ... for every thread's copies; period p-1's buffer is free
+        issue(p + 2);
+        if (p > 0) accumulate(vbuf + ((p - 1) & 1) * W * RL * 32);
+        vb = vbuf + (p & 1) * W * RL * 32;
+        if (rows) {
+            const float *src = stage + (p % 3) * CH * 32 + lane;
+            const int kbase = p * RL;
+            // warp-uniform: does any block of the warp need the tail handling?
+            const bool tail = kbase + RL > kc - W || __any_sync(0xffffffffu, live && kbase + RL > m - W);
+            if (p == 0) {
+                auto f = [&](auto PHc) { column(PHc, std::true_type{}, std::true_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            } else if (tail) {
+                auto f = [&](auto PHc) { column(PHc, std::false_type{}, std::true_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            } else {
+                auto f = [&](auto PHc) { column(PHc, std::false_type{}, std::false_type{}, src, kbase); };
+                StaticFor<0, RL>::run(f);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();  // (fused: the band warp is done too, bandres is final)
+    accumulate(vbuf + (PW & 1) * W * RL * 32);
+    // the corner: sums to shared memory [block][b][b2], then one thread per
+    // block factors C = A22 - S = L22 L22^T in FP64
+    float *sS = stage;  // the staging is free now
+    bsync();
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+        if (wq + NWARP * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+    bsync();
+    const bool live_end = FUSED ? (live && bandres[lane] == 0) : live;
+    if (tb < 32 && live_end) {
+        double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
+        double *outp = const_cast<double *>(out);
+        const PBandView v{outp + s_off[lane], outp + s_off[lane] + (int64_t)n * RL, n, W, m};
+        for (int i = 0; i < W; ++i)
+            for (int j = 0; j <= i; ++j) C[i * W + j] = v.a(m + i, m + j) - f32_to_f64_bits(sS[(lane * W + i) * W + j]);
+        int inf = 0;
+        for (int i = 0; i < W && inf == 0; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double sv = C[i * W + j];
+                for (int k = 0; k < j; ++k) sv -= C[i * W + k] * C[j * W + k];
+                if (j < i) {
+                    C[i * W + j] = sv / C[j * W + j];
+                } else {
+                    if (!(sv > 0.0)) {
+                        inf = m + i + 1;
+                        break;
+                    }
+                    C[i * W + i] = sqrt(sv);
+                }
+            }
+        }
+        for (int i = 0; i < W; ++i)
+            for (int j = 0; j <= i; ++j) v.put_b(i, m + j, C[i * W + j]);
+        binfo[lane] = inf;
+    }
+}
+
+template <int W, int WMIN, int NT, bool FUSED = false>
+struct F32BorderDispatch {
+    __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
+                               const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo,
+                               volatile int *prog = nullptr, const int *bandres = nullptr) {
+        if (w == W) {
+            f32_border<W, NT, FUSED>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog, bandres);
+            return;
+        }
+        F32BorderDispatch<W - 1, WMIN, NT, FUSED>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog,
+                                                       bandres);
+    }
+};
+template <int WMIN, int NT, bool FUSED>
+struct F32BorderDispatch<WMIN - 1, WMIN, NT, FUSED> {
+    __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
+                               const int *, const int *, float *, int *, volatile int * = nullptr,
+                               const int * = nullptr) {}
+};
+
+// floats: three staged periods, two periods of L21 values and the last W
+// columns of A21, W = 16
+constexpr int kF32BorderStage = 3 * 17 * 17 * 32 + 2 * 16 * 17 * 32 + 16 * 16 * 32;
+
+// Per-slice block table in shared memory: offsets, sizes, and whether the
+// block is still factored in FP32 (its band pass passed the pivot floor).
+struct SliceBlocks {
+    int64_t off[32];
+    int n[32], live[32], bi[32];
+};
+
+__device__ __forceinline__ void load_slice_blocks(SliceBlocks &t, const F32Slice &sl, const int32_t *items,
+                                                  const BlockDesc *blocks, const int32_t *info) {
+    // info == nullptr: every block of the slice counts as live
+    if (threadIdx.x < 32) {
+        const int L = threadIdx.x;
+        int64_t off = 0;
+        int n = 2 * sl.w + 2, live = 0, bi = 0;
+        if (L < sl.count) {
+            bi = items[sl.first + L];
+            const BlockDesc bd = blocks[bi];
+            off = bd.off_pband;
+            n = bd.n;
+            live = info ? info[bi] == 0 : 1;
+        }
+        t.off[L] = off;
+        t.n[L] = n;
+        t.live[L] = live;
+        t.bi[L] = bi;
+    }
+    __syncthreads();
+}
+
+
+// One CTA of NT threads per slice (256 or 512, the plan's border_threads):
+// warp q owns border rows R q .. R q + R-1, R = ceil(w / (NT / 32)).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_f32_border_pass(const F32Slice *__restrict__ slices,
+                                                        const int32_t *__restrict__ items,
+                                                        const BlockDesc *__restrict__ blocks,
+                                                        const float *__restrict__ sh, float *__restrict__ l21,
+                                                        const double *__restrict__ out, int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ SliceBlocks t;
+    __shared__ int binfo[32];
+    const F32Slice sl = slices[blockIdx.x];
+    load_slice_blocks(t, sl, items, blocks, info);
+    F32BorderDispatch<16, 1, NT>::run(sl.w, sl, sh + sl.sh, l21 + sl.l21, out, t.off, t.n, t.live, bsm, binfo);
+    if (threadIdx.x < 32 && t.live[threadIdx.x] && sl.w > 0) info[t.bi[threadIdx.x]] = binfo[threadIdx.x];
+}
+
+// -- launch helpers (one translation unit each) ---------------------------------
+// the separate border pass of slices [first, first+count), NT threads per CTA
+template <int NT>
+void launch_f32_border(sympix_plan_t pl, int first, int count, double *blocks, int32_t *info, cudaStream_t st);
+template <class A>
+void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue = 0);
+void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+void launch_f32_fused(sympix_plan_t pl, int nf, double *blocks, int32_t *info, cudaStream_t st);
+void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,
+                              cudaStream_t st);
+
+}  // namespace sympix
