@@ -158,7 +158,8 @@ struct sympix_plan_s {
     int max_w = 0;
     // sampling schedule (built once)
     std::vector<SampleItem> items_pband[5];  // buckets of WMAX = 8,16,32,64,128
-    std::vector<SampleItem> items_dense;
+    std::vector<SampleItem> items_dense;       // dense-format blocks with n <= 64: a warp per element
+    std::vector<SampleItem> items_dense_rows;  // larger ones: a thread per element, 256 per CTA
     std::vector<ConvItem> items_conv;  // every block in tiles of 128 pixels
     // factorisation work lists, each most expensive first: periodic band with
     // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16, [5] 16 < w <= 64;
@@ -186,7 +187,7 @@ struct sympix_plan_s {
     sympix::DevBuf<BlockDesc> d_blocks;
     sympix::DevBuf<PairEntry> d_entries;
     sympix::DevBuf<SampleItem> d_items_pband[5];
-    sympix::DevBuf<SampleItem> d_items_dense;
+    sympix::DevBuf<SampleItem> d_items_dense, d_items_dense_rows;
     sympix::DevBuf<ConvItem> d_items_conv;
     sympix::DevBuf<int32_t> d_factor_items[6];
     sympix::DevBuf<int32_t> d_f32_items;

@@ -310,7 +310,8 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     pl->size_dense = offd;
 
     // sampling work items: pband blocks in tiles of 128 columns, bucketed by
-    // band width; dense blocks in tiles of 8 elements (a warp each)
+    // band width; dense blocks of up to 64 pixels in tiles of 8 elements (a
+    // warp each), larger ones in tiles of 256 (a thread each)
     for (size_t b = 0; b < pl->blocks.size(); ++b) {
         const BlockDesc &bd = pl->blocks[b];
         if (bd.format == SYMPIX_BLOCK_PBAND) {
@@ -318,7 +319,10 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             for (int q0 = 0; q0 < bd.n; q0 += 128) pl->items_pband[bucket].push_back({(int32_t)b, q0});
         } else {
             const int64_t ne = (int64_t)bd.n * bd.n;
-            for (int64_t e0 = 0; e0 < ne; e0 += kDenseItemElems) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
+            if (bd.n <= 64)
+                for (int64_t e0 = 0; e0 < ne; e0 += kDenseItemElems) pl->items_dense.push_back({(int32_t)b, (int32_t)e0});
+            else
+                for (int64_t e0 = 0; e0 < ne; e0 += 256) pl->items_dense_rows.push_back({(int32_t)b, (int32_t)e0});
         }
     }
     // convolution work items: every block's ring in tiles of 128 pixels
@@ -393,7 +397,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         (rc = pl->d_shadow.alloc(pl->factor_items[5].empty() ? 1 : std::max<int64_t>(pl->size_pband, 1))))
         return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
-        (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_items_conv.upload(pl->items_conv)))
+        (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_items_dense_rows.upload(pl->items_dense_rows)) || (rc = pl->d_items_conv.upload(pl->items_conv)))
         return fail(rc);
     for (int bkt = 0; bkt < 5; ++bkt)
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
@@ -563,7 +567,7 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
         int chunks = 0;
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
-            op0 += left >= 4 ? 4 : left >= 2 ? 2 : 1;
+            op0 += left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
             ++chunks;
         }
         *table = 1 + (pl->nslots > 0 ? chunks : 0);
@@ -571,6 +575,7 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
     int s = sample_precision != SYMPIX_PREC_FP64 ? 1 : 0;  // the N^-1 split
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
+    s += pl->items_dense_rows.empty() ? 0 : 1;
     if (sample) *sample = s;
     // mirrors the launch sequence of sympix_factor_blocks
     int f = 0;

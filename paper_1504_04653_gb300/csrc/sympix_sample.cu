@@ -35,9 +35,10 @@ __global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, flo
 }
 
 // Small or wrapping blocks (every pixel pair of the ring may couple): one
-// warp per element (q, r), its lanes sharing the pixels of every coupled
-// ring, the separation index reduced to |dphi| <= pi; the partial sums meet
-// in a fixed-order shuffle tree.  FP64.
+// warp per element (q, r), its lanes sharing the pixels coupled to q on
+// every coupled ring (the arc |z_q| <= mmax, or the whole ring when the
+// support covers it), separation indices reduced to |dphi| <= pi; the
+// partial sums meet in a fixed-order shuffle tree.  FP64.
 
 __global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const SampleItem *__restrict__ items,
                                                                    const BlockDesc *__restrict__ blocks,
@@ -62,7 +63,68 @@ __global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const Sam
         const int64_t half = P * pe.nrho;  // P Q g
         const int64_t T2 = 2 * half;
         const double *trow = tb + tbase + pe.tab;
-        for (int p = lane; p < pe.nrho; p += 32) {
+        // the pixels coupled to q: the whole ring when the support covers it,
+        // else the arc |z_q| <= mmax (each pixel once)
+        const bool full = m >= half;
+        const int64_t Zq = (2 * (int64_t)q + 1) * Q;
+        int64_t lo = 0, hi = pe.nrho - 1;
+        if (!full) {  // ceil((Z - m - P) / 2P) .. floor((Z + m - P) / 2P)
+            const int64_t a = Zq - m - P, b = Zq + m - P, d2 = 2 * P;
+            lo = a >= 0 ? (a + d2 - 1) / d2 : -((-a) / d2);
+            hi = b >= 0 ? b / d2 : -((-b + d2 - 1) / d2);
+        }
+        for (int64_t pp = lo + lane; pp <= hi; pp += 32) {
+            int64_t pm = pp % pe.nrho;
+            if (pm < 0) pm += pe.nrho;
+            int64_t zq = (Zq - (2 * pm + 1) * P) % T2;
+            if (zq > half) zq -= T2;
+            if (zq <= -half) zq += T2;
+            if (zq > m || -zq > m) continue;
+            int64_t zr = ((2 * r + 1) * Q - (2 * pm + 1) * P) % T2;
+            if (zr > half) zr -= T2;
+            if (zr <= -half) zr += T2;
+            if (zr > m || -zr > m) continue;
+            const double bq = trow[((zq < 0 ? -zq : zq) - pe.par) >> 1];
+            const double br = trow[((zr < 0 ? -zr : zr) - pe.par) >> 1];
+            acc = fma(bq * nv[pe.noff + pm * pe.nstride], br, acc);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        int k = q > r ? q - r : r - q;
+        if (n - k < k) k = n - k;
+        if (k < bd.dK) acc += td[tbase + bd.dtab + k];
+        out[(dense_storage ? bd.off_dense : bd.off_pband) + (int64_t)q * n + r] = acc;
+    }
+}
+
+// Large dense-format blocks: one thread per element (q, r), 256 elements of
+// a row-major block per CTA, every pixel of every coupled ring tested (the
+// warp's 32 elements share their row q, so the q test is uniform), the
+// separation index reduced to |dphi| <= pi.  FP64.
+__global__ void __launch_bounds__(256) k_sample_dense_rows(const SampleItem *__restrict__ items,
+                                                      const BlockDesc *__restrict__ blocks,
+                                                      const PairEntry *__restrict__ entries, int64_t nslots,
+                                                      int64_t npix, const double *__restrict__ tb,
+                                                      const double *__restrict__ td, const double *__restrict__ ninv,
+                                                      double *__restrict__ out, int dense_storage) {
+    const SampleItem it = items[blockIdx.x];
+    const BlockDesc bd = blocks[it.block];
+    const int n = bd.n;
+    const int64_t eidx = (int64_t)it.q0 + threadIdx.x;
+    if (eidx >= (int64_t)n * n) return;
+    const int q = (int)(eidx / n), r = (int)(eidx % n);
+    const int64_t tbase = (int64_t)bd.op * nslots;
+    const double *nv = ninv + (int64_t)bd.op * npix;
+    double acc = 0.0;
+    for (int e = 0; e < bd.npairs; ++e) {
+        const PairEntry pe = entries[bd.pair0 + e];
+        const int64_t P = pe.P, Q = pe.Q, m = pe.mmax;
+        const int64_t half = P * pe.nrho;  // P Q g
+        const int64_t T2 = 2 * half;
+        const double *trow = tb + tbase + pe.tab;
+        for (int p = 0; p < pe.nrho; ++p) {
             int64_t zq = ((2 * q + 1) * Q - (2 * (int64_t)p + 1) * P) % T2;
             if (zq > half) zq -= T2;
             if (zq <= -half) zq += T2;
@@ -76,14 +138,10 @@ __global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const Sam
             acc = fma(bq * nv[pe.noff + (int64_t)p * pe.nstride], br, acc);
         }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) {
-        int k = q > r ? q - r : r - q;
-        if (n - k < k) k = n - k;
-        if (k < bd.dK) acc += td[tbase + bd.dtab + k];
-        out[(dense_storage ? bd.off_dense : bd.off_pband) + (int64_t)q * n + r] = acc;
-    }
+    int k = q > r ? q - r : r - q;
+    if (n - k < k) k = n - k;
+    if (k < bd.dK) acc += td[tbase + bd.dtab + k];
+    out[(dense_storage ? bd.off_dense : bd.off_pband) + (int64_t)q * n + r] = acc;
 }
 
 }  // namespace sympix
@@ -119,6 +177,10 @@ extern "C" int sympix_sample_blocks(sympix_plan_t pl, const double *ninv, int pr
     if (!pl->items_dense.empty())
         k_sample_dense<<<(unsigned)pl->items_dense.size(), 32 * kDenseItemElems, 0, st>>>(
             pl->d_items_dense.p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, pl->grid->npix, pl->d_tab_b.p,
+            pl->d_tab_d.p, ninv, blocks, dense ? 1 : 0);
+    if (!pl->items_dense_rows.empty())
+        k_sample_dense_rows<<<(unsigned)pl->items_dense_rows.size(), 256, 0, st>>>(
+            pl->d_items_dense_rows.p, pl->d_blocks.p, pl->d_entries.p, pl->nslots, pl->grid->npix, pl->d_tab_b.p,
             pl->d_tab_d.p, ninv, blocks, dense ? 1 : 0);
     trace_mark(pl, st, "k_sample_dense");
     cudaError_t e = cudaGetLastError();

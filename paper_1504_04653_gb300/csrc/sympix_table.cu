@@ -146,12 +146,14 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
         const unsigned grid = (unsigned)((pl->nslots + cta * kTableSpt - 1) / (cta * kTableSpt));
         for (int op0 = 0; op0 < pl->nops;) {
             const int left = pl->nops - op0;
-            const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+            const int chunk = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
 #define SPX_TABLE(NO)                                                                                              \
     k_table<NO><<<grid, cta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
                                       pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
-            if (chunk == 4)
+            if (chunk == 8)
+                SPX_TABLE(8);
+            else if (chunk == 4)
                 SPX_TABLE(4);
             else if (chunk == 2)
                 SPX_TABLE(2);
