@@ -275,7 +275,11 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
  *              (PBAND storage) a block whose pivots shrink below the plan's
  *              pivot floor (SYMPIX_OPT_FP32_PIVOT_FLOOR) relative to their
  *              original diagonal is near-degenerate and is refactored in FP64
- *              on the device.  Dense-format blocks (small or fully coupled
+ *              on the device, except that a band wider than 16 whose FP32
+ *              pivot falls to -1e-3 of its original diagonal or below fails
+ *              at that row without the refactor (the FP32 pivot is within
+ *              about (w+1) 2^-24 of the diagonal of the FP64 one, so FP64
+ *              fails there too; the block is left as sampled).  Dense-format blocks (small or fully coupled
  *              rings) are factored in FP64 always; with FP32X2, bands wider
  *              than 16 are factored in FP64.
  *   info       device int32 [nops * nblocks] (operator-major, blocks in ring

@@ -6,19 +6,80 @@
 namespace sympix {
 
 // ---------------------------------------------------------------------------
-// Wide bands (16 < w <= 64): one CTA per block.
+// Wide bands (16 < w <= 64): one CTA per block, the elimination state in
+// registers.
 //
-// The active band window (rows k..k+w, columns k..k+w), the w border rows at
-// columns k..k+w and the corner accumulator S live in shared memory; rows
-// and columns are stored at index mod (w+1), so moving the window to column
-// k+1 costs nothing: the slot of row/column k is reused for k+1+w.  Per
-// column: thread 0 forms the pivot, the threads scale the column (band and
-// border), then apply the rank-1 update to the band window, the border rows
-// and S while the next band row and border column, loaded one column ahead,
-// go into the freed slots.  T = double or float; the float version sends a
-// block whose pivot falls below the floor to the FP64 rescue.
+// The active band window (rows k..k+w, each with its columns row-w..row) and
+// the w border rows at columns k..k+w are stored by slot: row R and column C
+// sit at slots R mod (w+1) and C mod (w+1), so moving the window to column
+// k+1 only reuses the slot of row/column k for row/column k+1+w.  The
+// 2w+1 entries of a column slot (w+1 band rows by row slot, then the w
+// border rows) are split over G threads of kWideE consecutive entries each.
+//
+// One barrier per column.  Before the barrier of step k the group owning
+// column slot k mod (w+1) has published its raw column a = A(., k) (after
+// the updates of steps < k), 1/a_kk, sqrt(a_kk) and 1/sqrt(a_kk) to shared
+// memory; after it every thread applies A(R, C) -= a_R a_C / a_kk to its
+// entries (stale entries of eliminated columns take harmless garbage), the
+// new band row k+1+w and border column k+1+w go into the freed slot, and
+// the group of the next column publishes its column.  Every kWideKC columns
+// the CTA writes the finished columns of L = a / sqrt(a_kk) out together,
+// row by row.  Band rows and border columns arrive through a shared-memory
+// ring filled by cp.async kWideD steps ahead (FP32: converted once by the
+// thread that staged them).  After the band the corner
+// S = A22 - L21 L21^T is formed from the stored L21 in 4 x 4 register tiles
+// and factored in FP64 in shared memory.  T = double or float; the float
+// version sends a block whose pivot falls below the floor to the FP64
+// rescue.
 // ---------------------------------------------------------------------------
-constexpr int kWideMax = 64;
+constexpr int kWideD = 6;             // band rows staged ahead of the elimination
+constexpr int kWideNR = kWideD + 1;   // staging ring slots
+constexpr int kWideKC = 8;            // columns of L written out together
+constexpr int kWideNB = kWideKC + 1;  // raw-column buffers
+constexpr int kWideKS = 32;           // L21 columns per corner-update chunk
+
+// FP32 verdict on a band pivot that failed the floor test (row1 = its row
+// + 1): the FP32 pivot lies within about (w+1) 2^-24 of the original
+// diagonal of the FP64 one (every earlier pivot having passed the floor), so
+// a pivot at or below -1e-3 of the original diagonal is negative in FP64
+// too and fails the block at the same row; anything else is left to the
+// FP64 refactor.
+constexpr float kWideDecisive = 1e-3f;
+template <typename T>
+__device__ __forceinline__ int wide_verdict(T d, T od, int row1) {
+    if constexpr (sizeof(T) == 8)
+        return row1;
+    else
+        return d <= T(-kWideDecisive) * od ? row1 : kRescue;
+}
+
+// Shared-memory layout of a wide CTA (byte offsets) for band width w and
+// element size tsz.
+struct WideLayout {
+    int S, NV, LP;
+    size_t la, piv, ring, ringt, corner, total;
+};
+__host__ __device__ inline size_t wide_al16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ inline WideLayout wide_layout(int w, int tsz) {
+    WideLayout L;
+    L.S = w + 1;
+    L.NV = 2 * w + 1;
+    L.LP = (L.NV + kWideE - 1) / kWideE * kWideE;
+    size_t o = 0;
+    L.la = o;  // kWideNB x LP raw columns
+    o = wide_al16(o + (size_t)kWideNB * L.LP * tsz);
+    L.piv = o;  // 1/a_kk, sqrt(a_kk), 1/sqrt(a_kk) per raw-column buffer
+    o = wide_al16(o + 3 * (size_t)kWideNB * tsz);
+    L.ring = o;  // kWideNR x LP staged FP64 rows
+    o = wide_al16(o + (size_t)kWideNR * L.LP * sizeof(double));
+    L.ringt = o;  // 2 x LP staged rows in T
+    o = wide_al16(o + 2 * (size_t)L.LP * tsz);
+    L.corner = o;  // L21 staging, then the w x w corner in FP64
+    const size_t a = (size_t)w * w * sizeof(double), b = (size_t)w * (kWideKS + 1) * tsz;
+    o = wide_al16(o + (a > b ? a : b));
+    L.total = o;
+    return L;
+}
 
 template <typename T>
 __device__ __forceinline__ T wide_from(double x);
@@ -28,6 +89,59 @@ template <>
 __device__ __forceinline__ float wide_from<float>(double x) { return f64_to_f32_bits(x); }
 __device__ __forceinline__ double wide_to(double x) { return x; }
 __device__ __forceinline__ double wide_to(float x) { return f32_to_f64_bits(x); }
+
+// kWideE consecutive entries from / to shared memory (16-byte aligned).
+__device__ __forceinline__ void wide_lds(const double *p, double (&r)[kWideE]) {
+#pragma unroll
+    for (int q = 0; q < kWideE / 2; ++q) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[q];
+        r[2 * q] = v.x;
+        r[2 * q + 1] = v.y;
+    }
+}
+__device__ __forceinline__ void wide_lds(const float *p, float (&r)[kWideE]) {
+#pragma unroll
+    for (int q = 0; q < kWideE / 4; ++q) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[q];
+        r[4 * q] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void wide_sts(double *p, const double (&r)[kWideE]) {
+#pragma unroll
+    for (int q = 0; q < kWideE / 2; ++q) reinterpret_cast<double2 *>(p)[q] = make_double2(r[2 * q], r[2 * q + 1]);
+}
+__device__ __forceinline__ void wide_sts(float *p, const float (&r)[kWideE]) {
+#pragma unroll
+    for (int q = 0; q < kWideE / 4; ++q)
+        reinterpret_cast<float4 *>(p)[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+}
+
+// x[e] = v / return x[e] for a run-time e in [LO, HI): a binary branch tree
+// (the owning lanes of a warp share e), not a select per register.
+template <int LO, int HI, typename T>
+__device__ __forceinline__ void wide_set(T (&x)[kWideE], int e, T v) {
+    if constexpr (HI - LO == 1) {
+        x[LO] = v;
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        if (e < MID)
+            wide_set<LO, MID>(x, e, v);
+        else
+            wide_set<MID, HI>(x, e, v);
+    }
+}
+template <int LO, int HI, typename T>
+__device__ __forceinline__ T wide_get(const T (&x)[kWideE], int e) {
+    if constexpr (HI - LO == 1) {
+        return x[LO];
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        return e < MID ? wide_get<LO, MID>(x, e) : wide_get<MID, HI>(x, e);
+    }
+}
 
 // Where the wide kernel writes L: straight into the FP64 blocks (FP64), or
 // into the FP32 band shadow, copied to the FP64 blocks only once the block
@@ -48,171 +162,300 @@ struct WideSink<float, View> {
     int n, w;
     __device__ void put_l(int i, int j, float x) const { band[(int64_t)i * (w + 1) + (i - j)] = x; }
     __device__ void put_b(int b, int j, float x) const { band[(int64_t)n * (w + 1) + (int64_t)b * n + j] = x; }
-    __device__ double get_b(int b, int j) const {
-        return f32_to_f64_bits(band[(int64_t)n * (w + 1) + (int64_t)b * n + j]);
-    }
+    __device__ float get_b(int b, int j) const { return band[(int64_t)n * (w + 1) + (int64_t)b * n + j]; }
 };
 
 template <typename T, bool DENSE>
-__global__ void __launch_bounds__(256) k_factor_wide(int nitems, const int32_t *__restrict__ items,
-                                                     const BlockDesc *__restrict__ blocks, double *__restrict__ out,
-                                                     int32_t *__restrict__ info, int rescue, float floor,
-                                                     float *__restrict__ shadow) {
-    extern __shared__ double wsm_raw[];
-    T *wsm = reinterpret_cast<T *>(wsm_raw);
+__global__ void __launch_bounds__(kWideMaxThreads)
+    k_factor_wide(int nitems, const int32_t *__restrict__ items, const BlockDesc *__restrict__ blocks,
+                  double *__restrict__ out, int32_t *__restrict__ info, int rescue, float floor,
+                  float *__restrict__ shadow) {
+    extern __shared__ __align__(16) unsigned char wsm[];
+    __shared__ int s_fail;
+    if ((int)blockIdx.x >= nitems) return;
     const int bi = items[blockIdx.x];
     if (rescue && info[bi] != kRescue) return;
     const BlockDesc bd = blocks[bi];
     typedef typename ViewOf<DENSE>::T View;
     const View v = ViewOf<DENSE>::make(out, bd);
-    const int w = bd.w, m = bd.n - bd.w, S = w + 1;
+    const int w = bd.w, n = bd.n, m = n - w;
+    const WideLayout lay = wide_layout(w, (int)sizeof(T));
+    const int S = lay.S, NV = lay.NV, LP = lay.LP, G = LP / kWideE;
     auto make_sink = [&]() {
         if constexpr (sizeof(T) == 4)
-            return WideSink<T, View>{shadow + bd.off_pband, bd.n, w};
+            return WideSink<T, View>{shadow + bd.off_pband, n, w};
         else
             return WideSink<T, View>{v};
     };
     const WideSink<T, View> sink = make_sink();
-    T *Wn = wsm;         // S x S, [row mod S][col mod S]
-    T *Bd = Wn + S * S;  // w x S, [b][col mod S]
-    T *Sc = Bd + w * S;  // w x w corner accumulator
-    T *lc = Sc + w * w;  // S: column k of L (band rows k..k+w)
-    T *lb = lc + S;      // w: column k of L (border rows)
-    T *od = lb + w;      // S: original diagonal of the window rows
-    __shared__ T piv;
-    __shared__ int fail;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < S * S; e += nt) {
-        const int r = e / S, c = e % S;
-        Wn[e] = (c <= r && r < m) ? wide_from<T>(v.a(r, c)) : T(0);
-        if (c == r) od[r] = Wn[e];
-    }
-    for (int e = tid; e < w * S; e += nt) {
-        const int b = e / S, c = e % S;
-        Bd[e] = c < m ? wide_from<T>(v.a(m + b, c)) : T(0);
-    }
-    for (int e = tid; e < w * w; e += nt) {
-        const int b = e / w, c = e % w;
-        Sc[e] = c <= b ? wide_from<T>(v.a(m + b, m + c)) : T(0);
-    }
-    if (tid == 0) fail = 0;
-    const int nband = w * (w + 1) / 2, nbord = w * w, ncorner = w * (w + 1) / 2;
-    const int e0 = nband + nbord + ncorner, total = e0 + S;
-    // the new-row element this thread stores each column (c < S), if any
-    int myc = -1;
-    for (int e = tid; e < total; e += nt)
-        if (e >= e0) myc = e - e0;
-    auto fetch = [&](int nc, T &pa, T &pb) {
-        pa = (myc >= 0 && nc < m) ? wide_from<T>(v.a(nc, nc - w + myc)) : T(0);
-        pb = (myc >= 0 && myc < w && nc < m) ? wide_from<T>(v.a(m + myc, nc)) : T(0);
+    T *la = reinterpret_cast<T *>(wsm + lay.la);
+    T *pinv = reinterpret_cast<T *>(wsm + lay.piv), *plkk = pinv + kWideNB, *prs = plkk + kWideNB;
+    double *ring = reinterpret_cast<double *>(wsm + lay.ring);
+    T *ringt = reinterpret_cast<T *>(wsm + lay.ringt);
+    double *csh = reinterpret_cast<double *>(wsm + lay.corner);
+    const int tid = threadIdx.x, nt = blockDim.x, nthr = G * S;
+    const int cs = tid / G, g = tid - cs * G, i0 = g * kWideE;
+    const bool live = tid < nthr;
+    const bool diag_owner = live && cs >= i0 && cs < i0 + kWideE;
+
+    // A(r, r - d) of band row r and A(m + b, r) of border row b, w < r < m
+    auto row_src = [&](int r, int d) -> const double * {
+        if constexpr (DENSE)
+            return v.p + (int64_t)r * n + (r - d);
+        else
+            return v.band + (int64_t)r * S + d;
     };
-    T pa, pb;
-    fetch(1 + w, pa, pb);
-    __syncthreads();
-    for (int k = 0; k < m; ++k) {
-        const int ks = k % S;
-        if (tid == 0) {
-            const T d = Wn[ks * S + ks];
-            if (!(d > T(floor) * od[ks])) {
-                fail = (sizeof(T) == 4) ? kRescue : k + 1;
-            } else {
-                const T lkk = sqrt(d);
-                piv = T(1) / lkk;
-                sink.put_l(k, k, lkk);
-            }
+    auto bord_src = [&](int b, int r) -> const double * {
+        if constexpr (DENSE) {
+            return v.p + (int64_t)(m + b) * n + r;
+        } else {
+            const int d = m + b - r;  // r > w > b: no wrapped entry
+            return d <= w ? v.band + (int64_t)(m + b) * S + d : nullptr;
         }
-        __syncthreads();
-        if (fail) break;
-        const T rs = piv;
-        for (int r = tid; r < S + w; r += nt) {
-            if (r == 0) {
-                lc[0] = T(0);
-            } else if (r <= w) {
-                const int row = k + r;
-                const T l = row < m ? Wn[(row % S) * S + ks] * rs : T(0);
-                lc[r] = l;
-                if (row < m) sink.put_l(row, k, l);
-            } else {
-                const int b = r - S;
-                const T l = Bd[b * S + ks] * rs;
-                lb[b] = l;
-                sink.put_b(b, k, l);
-            }
+    };
+    // the band row and border column entering the window at step kk
+    auto stage = [&](int kk) {
+        const int r = kk + 1 + w;
+        if (tid < NV) {
+            double *dst = ring + (kk % kWideNR) * LP + tid;
+            const double *src = nullptr;
+            if (r < m) src = tid < S ? row_src(r, tid) : bord_src(tid - S, r);
+            if (src)
+                cp_async8(dst, src);
+            else
+                *dst = 0.0;
         }
-        __syncthreads();
-        const int nc = k + 1 + w;
-        for (int e = tid; e < total; e += nt) {
+        cp_async_commit();
+    };
+    // the staged row of step kk in T (FP32: converted by the thread that
+    // staged it, once its copy has landed)
+    auto convert = [&](int kk) {
+        if constexpr (sizeof(T) == 4)
+            if (tid < NV) ringt[(kk & 1) * LP + tid] = wide_from<T>(ring[(kk % kWideNR) * LP + tid]);
+    };
+    // L columns [j0, j1) out of the raw-column buffers: band rows row by
+    // row (consecutive threads on consecutive columns of one row), then the
+    // border rows
+    auto flush = [&](int j0, int j1) {
+        const int nc = j1 - j0;
+        const int nband = (nc + w) * nc, nall = nband + w * nc;
+        for (int e = tid; e < nall; e += nt) {
             if (e < nband) {
-                int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f) + 1;
-                while (r * (r - 1) / 2 > e) --r;
-                while ((r + 1) * r / 2 <= e) ++r;
-                const int c = e - r * (r - 1) / 2 + 1;
-                const int row = k + r;
-                if (row < m) Wn[(row % S) * S + (k + c) % S] -= lc[r] * lc[c];
-            } else if (e < nband + nbord) {
-                const int f = e - nband, b = f / w, c = f % w + 1;
-                Bd[b * S + (k + c) % S] -= lb[b] * lc[c];
-            } else if (e < e0) {
-                const int f = e - nband - nbord;
-                int b = (int)((sqrtf(8.0f * f + 1.0f) - 1.0f) * 0.5f);
-                while (b * (b + 1) / 2 > f) --b;
-                while ((b + 1) * (b + 2) / 2 <= f) ++b;
-                const int c = f - b * (b + 1) / 2;
-                Sc[b * w + c] -= lb[b] * lb[c];
+                const int R = j0 + e / nc, j = j0 + e % nc, d = R - j;
+                if (d < 0 || d > w || R >= m) continue;
+                const int jb = j % kWideNB;
+                sink.put_l(R, j, d == 0 ? plkk[jb] : la[jb * LP + R % S] * prs[jb]);
             } else {
-                // band row nc (columns k+1..nc) and the border rows' column nc
-                // into the slot freed by row/column k
-                const int c = e - e0;
-                if (nc < m) {
-                    Wn[ks * S + (k + 1 + c) % S] = pa;
-                    if (c == w) od[ks] = pa;
-                }
-                if (c < w) Bd[c * S + ks] = pb;
+                const int f = e - nband, b = f / nc, j = j0 + f % nc, jb = j % kWideNB;
+                sink.put_b(b, j, la[jb * LP + S + b] * prs[jb]);
             }
         }
-        fetch(nc + 1, pa, pb);
-        __syncthreads();
+    };
+
+    // window rows 0..w (row R's column at slot cs is cs, or cs - S < 0 before
+    // the start) and border columns 0..w
+    T x[kWideE];
+    T od = T(0);  // original diagonal of the row in slot cs (diag owner)
+#pragma unroll
+    for (int e = 0; e < kWideE; ++e) {
+        const int i = i0 + e;
+        T val = T(0);
+        if (live) {
+            if (i < S) {
+                const int C = cs <= i ? cs : cs - S;
+                if (C >= 0) val = wide_from<T>(v.a(i, C));
+            } else if (i < NV) {
+                val = wide_from<T>(v.a(m + i - S, cs));
+            }
+        }
+        x[e] = val;
+        if (i == cs) od = val;
     }
-    if (fail) {
-        if (tid == 0) info[bi] = fail;
-        return;
+    // column slot cs publishes column kn (after its updates) into buffer
+    // nb; its diagonal owner tests the pivot
+    auto publish = [&](int kn, int nb) {
+        wide_sts(la + nb * LP + i0, x);
+        if (diag_owner) {
+            const T dn = wide_get<0, kWideE>(x, cs - i0);
+            if (!(dn > T(floor) * od)) {
+                s_fail = wide_verdict(dn, od, kn + 1);
+            } else {
+                const T lkk = sqrt(dn);
+                pinv[nb] = T(1) / dn;
+                plkk[nb] = lkk;
+                prs[nb] = T(1) / lkk;
+            }
+        }
+    };
+    // padding of the staging rows stays zero
+    for (int e = tid; e < kWideNR * LP; e += nt)
+        if (e % LP >= NV) ring[e] = 0.0;
+    for (int e = tid; e < 2 * LP; e += nt)
+        if (e % LP >= NV) ringt[e] = T(0);
+    for (int kk = 0; kk < kWideD; ++kk) stage(kk);
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (live && cs == 0) publish(0, 0);
+    cp_async_wait<kWideD - 1>();
+    convert(0);
+
+    int ks = 0, rslot = 0, kb = 0, kflush = 0;
+    for (int k = 0; k < m; ++k) {
+        __syncthreads();  // column k, its pivot values and the staged row k are in place
+        if (s_fail) break;
+        const T *lk = la + kb * LP;
+        int kb1 = kb + 1;
+        if (kb1 == kWideNB) kb1 = 0;
+        if (live) {
+            // rank-1 update of this thread's entries
+            const T t = lk[cs] * pinv[kb];
+            T a[kWideE];
+            wide_lds(lk + i0, a);
+#pragma unroll
+            for (int e = 0; e < kWideE; ++e) x[e] = fma(-a[e], t, x[e]);
+            // column slot ks becomes column k+1+w: its border rows take the
+            // staged column (its band entries are stale, the one of row slot
+            // ks is set next); row slot ks of every column slot takes the
+            // staged band row k+1+w
+            const T *rg;
+            if constexpr (sizeof(T) == 4)
+                rg = ringt + (k & 1) * LP;
+            else
+                rg = ring + rslot * LP;
+            if (cs == ks) wide_lds(rg + i0, x);
+            if (ks >= i0 && ks < i0 + kWideE) {
+                int dd = ks - cs;
+                if (dd < 0) dd += S;
+                const T val = rg[dd];
+                wide_set<0, kWideE>(x, ks - i0, val);
+                if (cs == ks) od = val;
+            }
+            int c1 = ks + 1;
+            if (c1 == S) c1 = 0;
+            if (cs == c1 && k + 1 < m) publish(k + 1, kb1);
+        }
+        if (k + 1 - kflush == kWideKC) {
+            flush(kflush, k + 1);
+            kflush = k + 1;
+        }
+        stage(k + kWideD);
+        cp_async_wait<kWideD - 1>();
+        convert(k + 1);
+        if (++ks == S) ks = 0;
+        if (++rslot == kWideNR) rslot = 0;
+        kb = kb1;
     }
-    __shared__ int cinf;
-    if (tid == 0) {
-        // the w x w corner, FP64 arithmetic
-        int inf = 0;
-        for (int i = 0; i < w && inf == 0; ++i) {
-            for (int j = 0; j <= i; ++j) {
-                double s = wide_to(Sc[i * w + j]);
-                for (int q = 0; q < j; ++q) s -= sink.get_b(i, m + q) * sink.get_b(j, m + q);
-                if (j < i) {
-                    sink.put_b(i, m + j, T(s / sink.get_b(j, m + j)));
-                } else {
-                    if (!(s > 0.0)) {
-                        inf = m + i + 1;
-                        break;
+    cp_async_wait<0>();
+    int fail = s_fail;  // set before the last barrier the loop passed, or 0
+    if (!fail) {
+        if (kflush < m) flush(kflush, m);
+        // S = A22 - L21 L21^T from the stored L21, 4 x 4 tiles of the lower
+        // triangle, L21 staged kWideKS columns at a time
+        const int n4 = (w + 3) / 4, ntiles = n4 * (n4 + 1) / 2;
+        int tb = -1, tc = 0;
+        if (tid < ntiles) {
+            tb = (int)((sqrtf(8.0f * tid + 1.0f) - 1.0f) * 0.5f);
+            while (tb * (tb + 1) / 2 > tid) --tb;
+            while ((tb + 1) * (tb + 2) / 2 <= tid) ++tb;
+            tc = tid - tb * (tb + 1) / 2;
+        }
+        T acc[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+        T *stg = reinterpret_cast<T *>(csh);  // w x (kWideKS + 1)
+        for (int k0 = 0; k0 < m; k0 += kWideKS) {
+            const int kn = min(kWideKS, m - k0);
+            __syncthreads();  // L21 stored (first chunk) / the previous chunk used
+            for (int e = tid; e < w * kWideKS; e += nt) {
+                const int b = e / kWideKS, kk = e % kWideKS;
+                stg[b * (kWideKS + 1) + kk] = kk < kn ? sink.get_b(b, k0 + kk) : T(0);
+            }
+            __syncthreads();
+            if (tb >= 0) {
+                for (int kk = 0; kk < kn; ++kk) {
+                    T xa[4], xb[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const int ra = 4 * tb + p, rb = 4 * tc + p;
+                        xa[p] = ra < w ? stg[ra * (kWideKS + 1) + kk] : T(0);
+                        xb[p] = rb < w ? stg[rb * (kWideKS + 1) + kk] : T(0);
                     }
-                    sink.put_b(i, m + i, T(sqrt(s)));
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fma(xa[p], xb[q], acc[p][q]);
                 }
             }
         }
-        if (sizeof(T) == 4 && inf) inf = kRescue;  // let FP64 decide
-        cinf = inf;
-        info[bi] = inf;
-    }
-    if constexpr (sizeof(T) == 4) {
-        // the block factored in FP32: copy L from the shadow
-        __syncthreads();
-        if (cinf) return;
-        const int64_t nb = (int64_t)m * S;  // band rows < m
-        for (int64_t e = tid; e < nb; e += nt) {
-            const int row = (int)(e / S), d = (int)(e % S);
-            if (d <= row) out[bd.off_pband + e] = f32_to_f64_bits(sink.band[e]);
+        __syncthreads();  // staging done: the corner goes where it was
+        if (tb >= 0) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * tb + p, j = 4 * tc + q;
+                    if (i < w && j <= i) csh[i * w + j] = v.a(m + i, m + j) - wide_to(acc[p][q]);
+                }
         }
-        const int64_t bo = (int64_t)bd.n * S;
-        for (int64_t e = tid; e < (int64_t)w * bd.n; e += nt) {
-            const int b = (int)(e / bd.n), j = (int)(e % bd.n);
-            if (j <= m + b) out[bd.off_pband + bo + e] = f32_to_f64_bits(sink.band[bo + e]);
+        __syncthreads();
+        // the corner, factored in FP64 in shared memory (right-looking)
+        for (int j = 0; j < w; ++j) {
+            if (tid == 0) {
+                const double dj = csh[j * w + j];
+                if (!(dj > 0.0))
+                    s_fail = sizeof(T) == 4 ? kRescue : m + j + 1;  // the FP32 path lets FP64 decide
+                else
+                    csh[j * w + j] = sqrt(dj);
+            }
+            __syncthreads();
+            if (s_fail) break;
+            const double ljj = csh[j * w + j];
+            for (int i = j + 1 + tid; i < w; i += nt) csh[i * w + j] /= ljj;
+            __syncthreads();
+            const int nr = w - j - 1;
+            for (int e = tid; e < nr * nr; e += nt) {
+                const int i = j + 1 + e / nr, c = j + 1 + e % nr;
+                if (c <= i) csh[i * w + c] -= csh[i * w + j] * csh[c * w + j];
+            }
+            __syncthreads();
+        }
+        fail = s_fail;
+        if (!fail)
+            for (int e = tid; e < w * w; e += nt) {
+                const int b = e / w, c = e % w;
+                if (c <= b) sink.put_b(b, m + c, T(csh[e]));
+            }
+    }
+    if (tid == 0) info[bi] = fail;
+    if constexpr (sizeof(T) == 4) {
+        // the block factored in FP32: copy L from the shadow, rows of the
+        // band (d <= row) then the border (columns <= m + b)
+        if (fail) return;
+        __syncthreads();
+        const float *sb = sink.band;
+        double *ob = out + bd.off_pband;
+        const int dq = nt / S, dr = nt % S;
+        for (int row = tid / S, d = tid % S; row < m;) {
+            if (d <= row) ob[(int64_t)row * S + d] = f32_to_f64_bits(sb[(int64_t)row * S + d]);
+            row += dq;
+            d += dr;
+            if (d >= S) {
+                d -= S;
+                ++row;
+            }
+        }
+        const int64_t bo = (int64_t)n * S;
+        const int eq = nt / n, er = nt % n;
+        for (int b = tid / n, j = tid % n; b < w;) {
+            if (j <= m + b) ob[bo + (int64_t)b * n + j] = f32_to_f64_bits(sb[bo + (int64_t)b * n + j]);
+            b += eq;
+            j += er;
+            if (j >= n) {
+                j -= n;
+                ++b;
+            }
         }
     }
 }
@@ -380,27 +623,28 @@ void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, doubl
                               cudaStream_t st) {
     const int nw = (int)pl->factor_items[5].size();
     if (nw) {
-        const size_t smem = (size_t)((kWideMax + 1) * (kWideMax + 1) + kWideMax * (kWideMax + 1) +
-                                     kWideMax * kWideMax + 3 * (kWideMax + 1)) *
-                            sizeof(double);
-        const int32_t *it = pl->d_factor_items[5].p;
         // FP32 arithmetic for the FP32 factor (near-degenerate blocks then
-        // rescued in FP64), FP64 otherwise
+        // rescued in FP64), FP64 otherwise; one launch per CTA size
+        auto launch = [&](auto kern, size_t tsz, int rescue, float floor) {
+            for (const WideClass &c : pl->wide_cls) {
+                const size_t smem = wide_layout(c.wmax, (int)tsz).total;
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<(unsigned)c.count, (unsigned)c.threads, smem, st>>>(
+                    c.count, pl->d_factor_items[5].p + c.begin, pl->d_blocks.p, blocks, info, rescue, floor,
+                    pl->d_shadow.p);
+            }
+        };
+        auto kd = dense ? k_factor_wide<double, true> : k_factor_wide<double, false>;
         if (precision == SYMPIX_PREC_FP32 && !dense) {
-            auto kf = k_factor_wide<float, false>;
-            auto kd = dense ? k_factor_wide<double, true> : k_factor_wide<double, false>;
-            cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            kf<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 0, (float)pl->fp32_pivot_floor,
-                                      pl->d_shadow.p);
-            kd<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 1, 0.0f, nullptr);
+            launch(k_factor_wide<float, false>, sizeof(float), 0, (float)pl->fp32_pivot_floor);
+            trace_mark(pl, st, "k_factor_wide");
+            launch(kd, sizeof(double), 1, 0.0f);
+            trace_mark(pl, st, "k_factor_wide_rescue");
         } else {
-            auto kd = dense ? k_factor_wide<double, true> : k_factor_wide<double, false>;
-            cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            kd<<<nw, 256, smem, st>>>(nw, it, pl->d_blocks.p, blocks, info, 0, 0.0f, nullptr);
+            launch(kd, sizeof(double), 0, 0.0f);
+            trace_mark(pl, st, "k_factor_wide");
         }
     }
-    if (nw) trace_mark(pl, st, "k_factor_wide");
     const int nd = (int)pl->factor_items[3].size(), ns = (int)pl->factor_items[4].size();
     if (nd)
         k_factor_dense<<<(unsigned)((nd * 32 + 127) / 128), 128, 0, st>>>(nd, pl->d_factor_items[3].p, pl->d_blocks.p,

@@ -33,6 +33,21 @@ constexpr int kDenseItemElems = 8;
 // Elements per block in one CTA of the FP32 shadow transposes (x 32 blocks).
 constexpr int kTileE = 128;
 
+// Wide-band factor kernel (16 < w <= 64): each thread holds kWideE entries of
+// one column slot of the window (G = ceil((2w+1) / kWideE) threads per slot,
+// w+1 slots); CTAs of up to kWideMaxThreads threads.
+constexpr int kWideE = 24;
+constexpr int kWideMaxThreads = 416;
+inline int wide_threads(int w) {
+    const int t = (2 * w + 1 + kWideE - 1) / kWideE * (w + 1);
+    return t;
+}
+// One launch of the wide kernel: items [begin, begin + count) of list 5,
+// CTAs of `threads`, shared memory sized for the widest band `wmax`.
+struct WideClass {
+    int begin, count, threads, wmax;
+};
+
 // FP64 [count] -> FP32 hi and lo planes (integer-ALU split; sympix_sample.cu).
 __global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, float *__restrict__ n32,
                              float *__restrict__ nlo);
@@ -165,6 +180,7 @@ struct sympix_plan_s {
     // [0] w <= 8, [1] 8 < w <= 12, [2] 12 < w <= 16, [5] 16 < w <= 64;
     // [3] dense format with n <= 1024; [4] everything else
     std::vector<int32_t> factor_items[6];
+    std::vector<sympix::WideClass> wide_cls;  // list 5 by CTA size
     // FP32 factorisation on a band shadow: periodic-band blocks with w <= 16
     // grouped by exact width into slices of up to 32 blocks; each slice's
     // shadow is lane-interleaved (element e of its block L at 32 e + L)

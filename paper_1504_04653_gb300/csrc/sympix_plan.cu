@@ -349,6 +349,25 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             list = bd.n <= 1024 ? 3 : 4;
         pl->factor_items[list].push_back(b);
     }
+    // wide bands: one launch per CTA size (a multiple of 32 threads, capped),
+    // most expensive blocks first within each
+    {
+        auto &l5 = pl->factor_items[5];
+        auto cta = [&](int b) {
+            const int t = (wide_threads(pl->blocks[b].w) + 31) / 32 * 32;
+            return std::min(t, kWideMaxThreads);
+        };
+        std::stable_sort(l5.begin(), l5.end(), [&](int x, int y) { return cta(x) > cta(y); });
+        pl->wide_cls.clear();
+        for (size_t i = 0; i < l5.size(); ++i) {
+            const int t = cta(l5[i]);
+            if (pl->wide_cls.empty() || pl->wide_cls.back().threads != t)
+                pl->wide_cls.push_back({(int)i, 0, t, 0});
+            WideClass &c = pl->wide_cls.back();
+            ++c.count;
+            c.wmax = std::max(c.wmax, pl->blocks[l5[i]].w);
+        }
+    }
 
     // FP32 factorisation on a band shadow: blocks by exact width (most
     // expensive first, so a slice holds blocks of similar length), slices of
@@ -596,7 +615,7 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
     } else {
         f = (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
     }
-    if (!pl->factor_items[5].empty()) f += (factor_precision == SYMPIX_PREC_FP32 && pband) ? 2 : 1;
+    f += (int)pl->wide_cls.size() * ((factor_precision == SYMPIX_PREC_FP32 && pband) ? 2 : 1);
     for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
     if (factor) *factor = f;
     return SYMPIX_OK;

@@ -381,6 +381,44 @@ def test_batched_wide_operators(S, dev, precision):
                 assert _err(L @ L.T, ref) <= 10 * tol, (o, j, _err(L @ L.T, ref))
 
 
+@pytest.mark.parametrize("precision,storage", [("fp64", "pband"), ("fp32", "pband"), ("fp64", "dense")])
+def test_wide_factor_every_block(S, dev, precision, storage):
+    """Every block of band width 16 < w <= 64 (the wide-band factor, one CTA
+    per block): L L^T against the sampled block, and info against numpy's
+    Cholesky of the same block."""
+    radii = np.linspace(0.22, 0.85, 6)  # block band widths from 17 to 64 and beyond at l_max = 120
+    wl = W.Workload("wide120", 120, [600.0] * 6, [0.0, 5.0, 10.0, 15.0, 20.0, 25.0], list(range(61, 67)))
+    r = _run(S, dev, wl, precision="fp64", storage=storage, factor=True, factor_precision=precision,
+             radii=radii)
+    plan, nr = r["plan"], int(r["grid"].nrings)
+    info64 = None
+    if precision != "fp64":  # the verdicts must be FP64's, row for row
+        import torch
+        again = torch.tensor(r["sampled"], dtype=torch.float64, device=dev)
+        info64 = S.sympix_factor_blocks(plan, again, storage=storage, precision="fp64").cpu().numpy()
+    seen = set()
+    for o in range(6):
+        for j in range(nr):
+            _, n, w, fmt = plan.block_layout("pband", o, j)
+            if fmt != S.BLOCK_PBAND or not 16 < w <= 64:
+                continue
+            seen.add(int(w))
+            M = S.unpack_block(r["sampled"], plan, storage, o, j)
+            try:
+                np.linalg.cholesky(M)
+                ok = True
+            except np.linalg.LinAlgError:
+                ok = False
+            info = int(r["info"][o * nr + j])
+            assert (info == 0) == ok, (o, j, n, w, info)
+            if info64 is not None:
+                assert info == int(info64[o * nr + j]), (o, j, n, w, info, int(info64[o * nr + j]))
+            if ok:
+                L = S.unpack_block(r["factored"], plan, storage, o, j, factored=True)
+                assert _err(L @ L.T, M) <= 10 * TOL[precision], (o, j, n, w, _err(L @ L.T, M))
+    assert len(seen) >= 20 and max(seen) >= 60, sorted(seen)
+
+
 # -- pixel-domain convolution g = B^ f (Eq. convolution-pixel) --------------------
 
 def _pixel_ring_col(grid):
