@@ -395,31 +395,66 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
             }
         }
     };
-    // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b: the
-    // W (W+1)/2 pairs are dealt round-robin to the warps, lane = block;
-    // each period's L21 values pass through vbuf
+    // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b, lane =
+    // block; each period's L21 values pass through vbuf.  With one border
+    // row per warp (R = 1) a pair goes to the warp owning one of its rows
+    // (b when b + b2 is odd or b = b2, else b2), which takes that operand
+    // from its own registers: one shared load per FMA, about (W+1)/2 + 1
+    // pairs per warp.  Otherwise the pairs are dealt round-robin.
     constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + NWARP - 1) / NWARP;
+    constexpr bool OWN = R == 1;
+    constexpr int NPC = OWN ? (W + 1) / 2 + 1 : (NP > 0 ? NP : 1);
     const int wq = tb >> 5;
-    int pb[NP > 0 ? NP : 1], pb2[NP > 0 ? NP : 1];
-    float sacc[NP > 0 ? NP : 1];
+    int pb[NPC], pb2[NPC], po[NPC];
+    float sacc[NPC];
+    int npw = 0;  // pairs of this warp
+    if constexpr (OWN) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        int j = wq + NWARP * i, bb = 0;
-        while (j > bb) {  // pair j = bb (bb+1)/2 + b2
-            j -= bb + 1;
-            ++bb;
+        for (int i = 0; i < NPC; ++i) {
+            pb[i] = pb2[i] = po[i] = 0;
+            sacc[i] = 0.0f;
         }
-        pb[i] = bb < W ? bb : 0;
-        pb2[i] = bb < W ? j : 0;
-        sacc[i] = 0.0f;
+        for (int bb = 0; bb < W; ++bb)
+            for (int b2 = 0; b2 <= bb; ++b2) {
+                const int owner = (bb == b2 || ((bb + b2) & 1)) ? bb : b2;
+                if (owner != wq) continue;
+#pragma unroll
+                for (int i = 0; i < NPC; ++i)
+                    if (i == npw) {
+                        pb[i] = bb;
+                        pb2[i] = b2;
+                        po[i] = bb == wq ? b2 : bb;
+                    }
+                ++npw;
+            }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NPC; ++i) {
+            int j = wq + NWARP * i, bb = 0;
+            while (j > bb) {  // pair j = bb (bb+1)/2 + b2
+                j -= bb + 1;
+                ++bb;
+            }
+            pb[i] = bb < W ? bb : 0;
+            pb2[i] = bb < W ? j : 0;
+            po[i] = 0;
+            sacc[i] = 0.0f;
+            if (wq + NWARP * i < NPAIR) npw = i + 1;
+        }
     }
     auto accumulate = [&](const float *v) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            if (wq + NWARP * i >= NPAIR) break;
-            const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
+        for (int i = 0; i < NPC; ++i) {
+            if (i >= npw) break;
+            if constexpr (OWN) {
+                const float *z = v + po[i] * RL * 32 + lane;
 #pragma unroll
-            for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+                for (int c = 0; c < RL; ++c) sacc[i] = fmaf(y[0][c], z[c * 32], sacc[i]);
+            } else {
+                const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+            }
         }
     };
     issue(0);
@@ -456,8 +491,8 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     float *sS = stage;  // the staging is free now
     bsync();
 #pragma unroll
-    for (int i = 0; i < NP; ++i)
-        if (wq + NWARP * i < NPAIR) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+    for (int i = 0; i < NPC; ++i)
+        if (i < npw) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
     bsync();
     const bool live_end = FUSED ? (live && bandres[lane] == 0) : live;
     if (tb < 32 && live_end) {
