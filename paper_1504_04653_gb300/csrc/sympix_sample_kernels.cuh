@@ -119,19 +119,53 @@ struct SameCount<A, WMAX, 0> {
 };
 
 // Any ring pair: for each stored offset d (static) the pixels coupled to both
-// q and q - d form one contiguous run, (2p+1)P in [Z - m, Z - 2dQ + m].
-template <class A, int WMAX>
+// q and q - d form one contiguous run, (2p+1)P in [Z - m, Z - 2dQ + m]: a
+// prefix of q's own arc (d = 0).  With a cache (this thread's column of a
+// shared array, stride 128) the weights b(q, p) N^-1_p of the arc are formed
+// once, in the same rounding, and every d walks its prefix of them; arcs
+// longer than the cache take the direct walk.
+constexpr int kArcCache = 88;  // cached arc length per thread (FP32, w > 16; 44 KB per CTA)
+
+template <class A, int WMAX, bool CACHE>
 __device__ __forceinline__ void general_entry(typename A::V (&acc)[WMAX + 1], int q, int w, const PairEntry &pe,
                                               const double *__restrict__ n64, const float *__restrict__ n32,
                                               const float *__restrict__ nlo, const double *__restrict__ tb,
                                               const float *__restrict__ tb32, const float *__restrict__ tblo,
-                                              int64_t tab) {
+                                              int64_t tab, typename A::V *wc) {
     typedef typename A::V V;
     const int P = pe.P, Q = pe.Q, m = pe.mmax, par = pe.par;
     const int Z = (2 * q + 1) * Q;
     const int p_lo = ceil_div(Z - m - P, 2 * P);
     int pm0 = p_lo % pe.nrho;
     if (pm0 < 0) pm0 += pe.nrho;
+    if constexpr (CACHE) {
+        const int narc = floor_div(Z + m - P, 2 * P) - p_lo + 1;
+        if (narc <= kArcCache) {
+            int pm = pm0, z = Z - (2 * p_lo + 1) * P;
+            for (int j = 0; j < narc; ++j) {
+                const int lq = (abs(z) - par) >> 1;
+                wc[j * 128] = A::mul(A::tab(tb, tb32, tblo, tab + lq),
+                                     A::nval(n64, n32, nlo, pe.noff + (int64_t)pm * pe.nstride));
+                z -= 2 * P;
+                if (++pm == pe.nrho) pm = 0;
+            }
+#pragma unroll
+            for (int d = 0; d <= WMAX; ++d) {
+                if (d > w || 2 * d * Q > 2 * m) break;
+                const int cnt = floor_div(Z - 2 * d * Q + m - P, 2 * P) - p_lo + 1;
+                int zd = Z - 2 * d * Q - (2 * p_lo + 1) * P;
+                V a = A::zero();
+#pragma unroll 4
+                for (int j = 0; j < cnt; ++j) {
+                    const int lr = (abs(zd) - par) >> 1;
+                    a = A::fma_(wc[j * 128], A::tab(tb, tb32, tblo, tab + lr), a);
+                    zd -= 2 * P;
+                }
+                acc[d] = A::add(acc[d], a);
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int d = 0; d <= WMAX; ++d) {
         if (d > w || 2 * d * Q > 2 * m) break;
@@ -168,7 +202,10 @@ __global__ void __launch_bounds__(128) k_sample_pband(const SampleItem *__restri
     constexpr int KCAP = PREC == 1 ? 17 : 9;
     constexpr int KTOP = (WMAX / 2 + 1) < KCAP ? (WMAX / 2 + 1) : KCAP;
     constexpr bool STAGE = !DENSE_OUT && WMAX <= 16;
+    constexpr bool CACHE = PREC == 1 && WMAX > 16;  // arc weights in dynamic shared memory
     __shared__ double stage[STAGE ? 128 * (WMAX + 1) : 1];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    V *wc = reinterpret_cast<V *>(dyn_smem) + threadIdx.x;
     const SampleItem it = items[blockIdx.x];
     const BlockDesc bd = blocks[it.block];
     const int q = it.q0 + (int)threadIdx.x;
@@ -191,7 +228,7 @@ __global__ void __launch_bounds__(128) k_sample_pband(const SampleItem *__restri
             if (pe.P == 1 && pe.Q == 1)
                 done = SameCount<A, WMAX, KTOP>::run(pe.mmax / 2 + 1, acc, q, n, w, n64 + pe.noff, n32 + pe.noff,
                                                      nlo + pe.noff, pe.nstride, tb, tb32, tblo, tab);
-            if (!done) general_entry<A, WMAX>(acc, q, w, pe, n64, n32, nlo, tb, tb32, tblo, tab);
+            if (!done) general_entry<A, WMAX, CACHE>(acc, q, w, pe, n64, n32, nlo, tb, tb32, tblo, tab, wc);
         }
         // D^ on the same ring, in the contraction's arithmetic
 #pragma unroll
@@ -343,8 +380,11 @@ __global__ void __launch_bounds__(64) k_sample_pband_f32x2(const SampleItem *__r
                     a0[d] = acc[d].x;
                     a1[d] = acc[d].y;
                 }
-                general_entry<Arith<1>, WMAX>(a0, q, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr, tab);
-                if (live1) general_entry<Arith<1>, WMAX>(a1, q + 1, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr, tab);
+                general_entry<Arith<1>, WMAX, false>(a0, q, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr, tab,
+                                                     nullptr);
+                if (live1)
+                    general_entry<Arith<1>, WMAX, false>(a1, q + 1, w, pe, nullptr, n32, nullptr, nullptr, tb32, nullptr,
+                                                         tab, nullptr);
 #pragma unroll
                 for (int d = 0; d <= WMAX; ++d) acc[d] = make_float2(a0[d], a1[d]);
             }
@@ -388,11 +428,13 @@ void launch_pband(sympix_plan_t pl, const double *ninv, double *blocks, cudaStre
                                             pl->d_tab_b32.p, pl->d_tab_d32.p, pl->d_ninv32.p, blocks);
             continue;
         }
+        // FP32 wide bands: the arc-weight cache (kArcCache floats per thread)
+        const size_t wcs = PREC == 1 ? (size_t)128 * kArcCache * sizeof(float) : 0;
         switch (wm[b]) {
             case 8: k_sample_pband<PREC, 8, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
             case 16: k_sample_pband<PREC, 16, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
-            case 32: k_sample_pband<PREC, 32, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
-            default: k_sample_pband<PREC, 64, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
+            case 32: k_sample_pband<PREC, 32, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS); break;
+            default: k_sample_pband<PREC, 64, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS); break;
         }
 #undef SPX_ARGS
     }
