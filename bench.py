@@ -167,8 +167,8 @@ ALU_PEAK = {"fp64": (FP64_NOMINAL, "nominal FP64 1.25 TFLOP/s (a DFMA probe meas
 # profiles/; an entry is removed when its kernel changes.
 TRAFFIC = {
     # profiles/dram_lmax3000_mixed_step.md
-    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_fused"): 1641800000,
-    ("lmax3000_fwhm5", "fp32:fp32", "k_table"): 800000,
+    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_fused"): 1669556992,
+    ("lmax3000_fwhm5", "fp32:fp32", "k_table"): 854528,
 }
 
 

@@ -124,7 +124,7 @@ struct SameCount<A, WMAX, 0> {
 // shared array, stride 128) the weights b(q, p) N^-1_p of the arc are formed
 // once, in the same rounding, and every d walks its prefix of them; arcs
 // longer than the cache take the direct walk.
-constexpr int kArcCache = 88;  // cached arc length per thread (FP32, w > 16; 44 KB per CTA)
+constexpr int kArcCache = 88;  // cached arc length per thread (w > 16; 44 KB per CTA in FP32, 88 KB else)
 
 template <class A, int WMAX, bool CACHE>
 __device__ __forceinline__ void general_entry(typename A::V (&acc)[WMAX + 1], int q, int w, const PairEntry &pe,
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) k_sample_pband(const SampleItem *__restri
     constexpr int KCAP = PREC == 1 ? 17 : 9;
     constexpr int KTOP = (WMAX / 2 + 1) < KCAP ? (WMAX / 2 + 1) : KCAP;
     constexpr bool STAGE = !DENSE_OUT && WMAX <= 16;
-    constexpr bool CACHE = PREC == 1 && WMAX > 16;  // arc weights in dynamic shared memory
+    constexpr bool CACHE = WMAX > 16;  // arc weights in dynamic shared memory
     __shared__ double stage[STAGE ? 128 * (WMAX + 1) : 1];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     V *wc = reinterpret_cast<V *>(dyn_smem) + threadIdx.x;
@@ -428,13 +428,21 @@ void launch_pband(sympix_plan_t pl, const double *ninv, double *blocks, cudaStre
                                             pl->d_tab_b32.p, pl->d_tab_d32.p, pl->d_ninv32.p, blocks);
             continue;
         }
-        // FP32 wide bands: the arc-weight cache (kArcCache floats per thread)
-        const size_t wcs = PREC == 1 ? (size_t)128 * kArcCache * sizeof(float) : 0;
+        // wide bands: the arc-weight cache, kArcCache values per thread
+        const size_t wcs = (size_t)128 * kArcCache * sizeof(typename Arith<PREC>::V);
         switch (wm[b]) {
             case 8: k_sample_pband<PREC, 8, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
             case 16: k_sample_pband<PREC, 16, DENSE_OUT><<<(unsigned)ni, 128, 0, st>>>(SPX_ARGS); break;
-            case 32: k_sample_pband<PREC, 32, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS); break;
-            default: k_sample_pband<PREC, 64, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS); break;
+            case 32:
+                cudaFuncSetAttribute(k_sample_pband<PREC, 32, DENSE_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wcs);
+                k_sample_pband<PREC, 32, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS);
+                break;
+            default:
+                cudaFuncSetAttribute(k_sample_pband<PREC, 64, DENSE_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wcs);
+                k_sample_pband<PREC, 64, DENSE_OUT><<<(unsigned)ni, 128, wcs, st>>>(SPX_ARGS);
+                break;
         }
 #undef SPX_ARGS
     }
