@@ -625,10 +625,15 @@ void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, doubl
     if (nw) {
         // FP32 arithmetic for the FP32 factor (near-degenerate blocks then
         // rescued in FP64), FP64 otherwise; one launch per CTA size
+        // the shared-memory limit is a property of the function, not of a
+        // launch: set it once to the largest class's need, so that every
+        // launch (and every node of a captured graph) stays within it
         auto launch = [&](auto kern, size_t tsz, int rescue, float floor) {
+            size_t smax = 0;
+            for (const WideClass &c : pl->wide_cls) smax = std::max(smax, wide_layout(c.wmax, (int)tsz).total);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
             for (const WideClass &c : pl->wide_cls) {
                 const size_t smem = wide_layout(c.wmax, (int)tsz).total;
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 kern<<<(unsigned)c.count, (unsigned)c.threads, smem, st>>>(
                     c.count, pl->d_factor_items[5].p + c.begin, pl->d_blocks.p, blocks, info, rescue, floor,
                     pl->d_shadow.p);

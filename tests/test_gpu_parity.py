@@ -419,6 +419,25 @@ def test_wide_factor_every_block(S, dev, precision, storage):
     assert len(seen) >= 20 and max(seen) >= 60, sorted(seen)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_wide_band_sampling_matches_oracle(S, dev, precision):
+    """Wide bands (w up to 64) next to rings of three times the pixel count:
+    the cached-arc walk and, for arcs longer than the cache, the direct walk
+    of the contraction, against the oracle's blocks."""
+    radii = np.linspace(0.22, 0.85, 6)
+    wl = W.Workload("wide120", 120, [600.0] * 6, [0.0, 5.0, 10.0, 15.0, 20.0, 25.0], list(range(61, 67)))
+    r = _run(S, dev, wl, precision=precision, radii=radii)
+    plan = r["plan"]
+    og = O.grid(wl.lmax)
+    widths = []
+    for o, j in ((0, 11), (1, 12), (1, 13), (2, 14), (3, 25), (5, 60)):
+        widths.append(plan.block_layout("pband", o, j)[2])
+        ref, _ = O.block(og, wl.beams()[o], wl.priors()[o], radii[o], r["ninv"][o], j)
+        M = S.unpack_block(r["sampled"], plan, "pband", o, j)
+        assert _err(M, ref) <= TOL[precision], (o, j, _err(M, ref))
+    assert max(widths) > 40, widths
+
+
 # -- pixel-domain convolution g = B^ f (Eq. convolution-pixel) --------------------
 
 def _pixel_ring_col(grid):
