@@ -34,12 +34,20 @@ __global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, flo
     nlo[i] = v.lo;
 }
 
+// z reduced to (-half, half] (T2 = 2 half): the longitude separation index
+// of a pixel pair on a pair of rings, as the kernel table is indexed.
+__device__ __forceinline__ int64_t wrap_half(int64_t z, int64_t half, int64_t T2) {
+    z %= T2;
+    if (z > half) z -= T2;
+    if (z <= -half) z += T2;
+    return z;
+}
+
 // Small or wrapping blocks (every pixel pair of the ring may couple): one
 // warp per element (q, r), its lanes sharing the pixels coupled to q on
 // every coupled ring (the arc |z_q| <= mmax, or the whole ring when the
 // support covers it), separation indices reduced to |dphi| <= pi; the
 // partial sums meet in a fixed-order shuffle tree.  FP64.
-
 __global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const SampleItem *__restrict__ items,
                                                                    const BlockDesc *__restrict__ blocks,
                                                                    const PairEntry *__restrict__ entries,
@@ -73,20 +81,27 @@ __global__ void __launch_bounds__(32 * kDenseItemElems) k_sample_dense(const Sam
             lo = a >= 0 ? (a + d2 - 1) / d2 : -((-a) / d2);
             hi = b >= 0 ? b / d2 : -((-b + d2 - 1) / d2);
         }
+        // z of q and of r against pixel pm, reduced to (-half, half]; the
+        // lane's next pixel is 32 on (mod nrho), so both z move by a fixed
+        // step reduced once
+        const int64_t nr = pe.nrho;
+        int64_t pm = (lo + lane) % nr;
+        if (pm < 0) pm += nr;
+        const int64_t s32 = 32 % nr, dz = 2 * P * s32;
+        int64_t zq = wrap_half(Zq - (2 * pm + 1) * P, half, T2);
+        int64_t zr = wrap_half((2 * (int64_t)r + 1) * Q - (2 * pm + 1) * P, half, T2);
         for (int64_t pp = lo + lane; pp <= hi; pp += 32) {
-            int64_t pm = pp % pe.nrho;
-            if (pm < 0) pm += pe.nrho;
-            int64_t zq = (Zq - (2 * pm + 1) * P) % T2;
-            if (zq > half) zq -= T2;
+            if (zq <= m && -zq <= m && zr <= m && -zr <= m) {
+                const double bq = trow[((zq < 0 ? -zq : zq) - pe.par) >> 1];
+                const double br = trow[((zr < 0 ? -zr : zr) - pe.par) >> 1];
+                acc = fma(bq * nv[pe.noff + pm * pe.nstride], br, acc);
+            }
+            pm += s32;
+            if (pm >= nr) pm -= nr;
+            zq -= dz;
             if (zq <= -half) zq += T2;
-            if (zq > m || -zq > m) continue;
-            int64_t zr = ((2 * r + 1) * Q - (2 * pm + 1) * P) % T2;
-            if (zr > half) zr -= T2;
+            zr -= dz;
             if (zr <= -half) zr += T2;
-            if (zr > m || -zr > m) continue;
-            const double bq = trow[((zq < 0 ? -zq : zq) - pe.par) >> 1];
-            const double br = trow[((zr < 0 ? -zr : zr) - pe.par) >> 1];
-            acc = fma(bq * nv[pe.noff + pm * pe.nstride], br, acc);
         }
     }
 #pragma unroll
@@ -124,18 +139,20 @@ __global__ void __launch_bounds__(256) k_sample_dense_rows(const SampleItem *__r
         const int64_t half = P * pe.nrho;  // P Q g
         const int64_t T2 = 2 * half;
         const double *trow = tb + tbase + pe.tab;
+        // z of q and of r against pixel p, reduced to (-half, half], moved
+        // by -2P per pixel
+        int64_t zq = wrap_half((2 * (int64_t)q + 1) * Q - P, half, T2);
+        int64_t zr = wrap_half((2 * (int64_t)r + 1) * Q - P, half, T2);
         for (int p = 0; p < pe.nrho; ++p) {
-            int64_t zq = ((2 * q + 1) * Q - (2 * (int64_t)p + 1) * P) % T2;
-            if (zq > half) zq -= T2;
+            if (zq <= m && -zq <= m && zr <= m && -zr <= m) {
+                const double bq = trow[((zq < 0 ? -zq : zq) - pe.par) >> 1];
+                const double br = trow[((zr < 0 ? -zr : zr) - pe.par) >> 1];
+                acc = fma(bq * nv[pe.noff + (int64_t)p * pe.nstride], br, acc);
+            }
+            zq -= 2 * P;
             if (zq <= -half) zq += T2;
-            if (zq > m || -zq > m) continue;
-            int64_t zr = ((2 * r + 1) * Q - (2 * (int64_t)p + 1) * P) % T2;
-            if (zr > half) zr -= T2;
+            zr -= 2 * P;
             if (zr <= -half) zr += T2;
-            if (zr > m || -zr > m) continue;
-            const double bq = trow[((zq < 0 ? -zq : zq) - pe.par) >> 1];
-            const double br = trow[((zr < 0 ? -zr : zr) - pe.par) >> 1];
-            acc = fma(bq * nv[pe.noff + (int64_t)p * pe.nstride], br, acc);
         }
     }
     int k = q > r ? q - r : r - q;
