@@ -37,15 +37,19 @@ __global__ void __launch_bounds__(128) k_convolve(const ConvItem *__restrict__ i
         const int64_t Z = (int64_t)(2 * q + 1) * pe.Q;
         const int64_t half = (int64_t)P * nr;
         if (m >= half) {
+            // z reduced to (-half, half] once, then moved by -2P per pixel
             const int64_t T2 = 2 * half;
+            int64_t z = (Z - (int64_t)P) % T2;
+            if (z > half) z -= T2;
+            if (z <= -half) z += T2;
             for (int p = 0; p < nr; ++p) {
-                int64_t z = (Z - (int64_t)(2 * p + 1) * P) % T2;
-                if (z > half) z -= T2;
+                if (z <= m && -z <= m) {
+                    const int lv = (int)(((z < 0 ? -z : z) - par) >> 1);
+                    acc = A::fma_(A::tab(tb, tb32, tblo, tab + lv),
+                                  A::nval(F64, F32, FLO, pe.noff + (int64_t)p * pe.nstride), acc);
+                }
+                z -= 2 * (int64_t)P;
                 if (z <= -half) z += T2;
-                if (z > m || -z > m) continue;
-                const int lv = (int)(((z < 0 ? -z : z) - par) >> 1);
-                acc = A::fma_(A::tab(tb, tb32, tblo, tab + lv), A::nval(F64, F32, FLO, pe.noff + (int64_t)p * pe.nstride),
-                              acc);
             }
         } else {
             // one contiguous arc; table and map read through per-pair bases,

@@ -570,14 +570,15 @@ def test_pband_storage_dense_format_large_blocks(S, dev):
             assert ok == (r["info"][k] == 0)
 
 
-def test_nine_operators_chunked_tables(S, dev):
-    """Nine operators share the recurrence in chunks (8 + 1): every
-    operator's blocks match the oracle with its own beam and prior."""
-    fwhm = [180.0, 200.0, 220.0, 240.0, 260.0, 280.0, 300.0, 320.0, 340.0]
-    wl = W.Workload("nine", 64, fwhm, [0.0] * 9, list(range(40, 49)))
+@pytest.mark.parametrize("nops", [9, 17])
+def test_chunked_tables(S, dev, nops):
+    """Operators share the recurrence in chunks (9 = 8 + 1, 17 = 8 + 8 + 1):
+    every operator's blocks match the oracle with its own beam and prior."""
+    fwhm = [180.0 + 20.0 * o for o in range(nops)]
+    wl = W.Workload("chunked", 64, fwhm, [0.0] * nops, list(range(40, 40 + nops)))
     r = _run(S, dev, wl, precision="fp64")
     og = O.grid(wl.lmax)
-    for o in range(9):
+    for o in range(nops):
         for j in (0, 20, 32):
             ref, _ = O.block(og, wl.beams()[o], wl.priors()[o], wl.radii()[o], r["ninv"][o], j)
             M = S.unpack_block(r["sampled"], r["plan"], "pband", o, j)
