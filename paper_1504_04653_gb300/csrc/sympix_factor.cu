@@ -18,8 +18,9 @@
 //   8 < w <= 16 (FP64, split FP32): one group of 32 lanes per block carries
 //       the band window and the border rows in registers, one column per
 //       step (band and border in one pass).
-//   16 < w <= 64: one CTA per block, window, border columns and S in shared
-//       memory indexed mod (w+1).
+//   16 < w <= 64: one CTA per block, the window and border rows in
+//       registers (24 entries of one column slot per thread), one barrier
+//       per column; the corner from the stored L21 at the end.
 //   dense-format blocks with n <= 1024: a warp per block, right-looking,
 //   FP64; larger ones: a CTA per block, blocked right-looking, FP64.
 //
