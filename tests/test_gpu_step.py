@@ -41,6 +41,35 @@ def _direct(plan, bl, dl, ninv, storage, sprec, fprec):
     return sampled.cpu().numpy(), blocks.cpu().numpy(), info.cpu().numpy()
 
 
+@pytest.mark.parametrize("storage,fprec", [("pband", "fp32"), ("pband", "fp64"), ("dense", "fp64")])
+def test_step_wide_bands_match_direct_calls(storage, fprec):
+    """Band widths 17..64 (the wide factor, one launch per CTA size and, for
+    FP32, an FP64 rescue launch per size): the captured step has as many
+    kernels as the plan says and replays the direct calls bit for bit."""
+    wl = W.Workload("wide120", 120, [262.0, 450.0, 640.0, 830.0, 1014.0], [0.0, 5.0, 10.0, 15.0, 20.0],
+                    [71, 72, 73, 74, 75])
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    dev = torch.device("cuda", 0)
+    bl = torch.tensor(wl.beams(), dtype=torch.float64, device=dev)
+    dl = torch.tensor(wl.priors(), dtype=torch.float64, device=dev)
+    ninv = torch.tensor(wl.ninv(colat), dtype=torch.float64, device=dev)
+    widths = {plan.block_layout("pband", o, j)[2] for o in range(wl.nops) for j in range(grid.nrings)
+              if plan.block_layout("pband", o, j)[3] == S.BLOCK_PBAND}
+    assert any(16 < w <= 32 for w in widths) and any(48 < w <= 64 for w in widths), sorted(widths)
+    s_ref, f_ref, i_ref = _direct(plan, bl, dl, ninv, storage, "fp64", fprec)
+    nbytes, _ = plan.blocks_size(storage)
+    blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
+    info = torch.full((plan.nblocks,), -7, dtype=torch.int32, device="cuda")
+    step = S.Step(plan, bl, dl, ninv, blocks, info, storage, "fp64", fprec)
+    assert step.kernels() == sum(plan.launches(storage, "fp64", fprec))
+    step.launch(S.STAGE_ALL)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocks.cpu().numpy(), f_ref)
+    assert np.array_equal(info.cpu().numpy(), i_ref)
+
+
 @pytest.mark.parametrize("name,storage,sprec,fprec", [
     ("lmax500", "pband", "fp32", "fp32"),
     ("lmax500", "pband", "fp64", "fp64"),
