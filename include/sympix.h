@@ -123,7 +123,10 @@ void sympix_grid_free(sympix_grid_t grid);
  *   r_s   host array [nops]: support radius (radians) of operator o; a pixel
  *         pair couples when its angular distance is <= r_s[o] (the truncation
  *         of Eq. f, one radius for D^ and B^ of the operator).  r_s >= pi
- *         couples every pair.
+ *         couples every pair.  A radius within 1e-12 (relative, in
+ *         1 - cos) of some pixel pair's separation is scaled by (1 - 1e-9)
+ *         first, so that no coupling decision rests on the last bits of a
+ *         sin (sympix_plan_radius reports the radius used).
  * The device computes, for every coupled pair of rings, the distinct pixel
  * separations (one symmetry class per distinct |phi_1 - phi_2|, shared by
  * the transposed and the north/south-mirrored ring pair) and the band width
@@ -145,6 +148,9 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           128 (default 32) */
 #define SYMPIX_OPT_BORDER_THREADS 4   /* threads per CTA of the FP32 border pass: 256 or 512
                                           (default 512) */
+#define SYMPIX_OPT_WAIT_LIMIT 5       /* polls of a bounded device wait (default 2^22, about
+                                          0.3 s): the FP32 factor's border warps wait for rows
+                                          the band warp of the same CTA publishes */
 
 /* Set a plan option; takes effect for the following calls on the plan. */
 int sympix_plan_option(sympix_plan_t plan, int option, double value);
@@ -203,6 +209,31 @@ int sympix_blocks_size(sympix_plan_t plan, int storage, size_t *bytes, int64_t *
  *   triangle (the strict upper triangle keeps M). */
 int sympix_block_layout(sympix_plan_t plan, int storage, int op, int ring, int64_t *offset,
                         int32_t *n, int32_t *w, int32_t *format);
+
+/* Device-side failures of the calls on a plan since the last query: waits
+ * for the work on `stream` (and what precedes it), then reads and clears
+ * the plan's device status word.  Returns SYMPIX_ETIMEOUT if a bounded wait
+ * ran out (the FP32 factor then also set info = -1 for the blocks whose
+ * factor it left incomplete), else SYMPIX_OK.  Synchronous.  The paper has
+ * no counterpart: this reports on the execution, not the method. */
+int sympix_plan_status(sympix_plan_t plan, void *stream);
+
+/* The support radius operator `op` is planned with, and its margin (either
+ * pointer may be NULL).  Coupling is the FP64 comparison
+ * u <= u_s = 2 sin^2(r_s / 2) with u = 1 - cos(gamma) (the truncation of
+ * Eq. f).  A pixel pair whose u lies within a few ulps of u_s could be
+ * decided either way by another correct implementation (another sin), so
+ * sympix_support measures, over every class of every coupled ring pair, the
+ * smallest relative distance |u - u_s| / u_s; while it is <= 1e-12 the
+ * radius is scaled by (1 - 1e-9) (at most 8 times).  *r_s receives the
+ * radius used (the caller's unless that happened), *margin the final
+ * smallest distance (+inf for r_s >= pi, where nothing is compared). */
+int sympix_plan_radius(sympix_plan_t plan, int op, double *r_s, double *margin);
+
+/* Device memory held by a plan (either pointer may be NULL): *bytes all of
+ * it, *staging the part sympix_kernel_table allocates on its first call
+ * (0 before that call).  For memory accounting and tests. */
+int sympix_plan_device_bytes(sympix_plan_t plan, size_t *bytes, size_t *staging);
 
 /* Per coupled ring pair (ring j of a planned block, neighbour ring rho):
  * the largest coupled separation index m (pixel pairs with
@@ -284,7 +315,9 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
  *              than 16 are factored in FP64.
  *   info       device int32 [nops * nblocks] (operator-major, blocks in ring
  *              order): 0, or i+1 for the first row i whose pivot is not
- *              positive (that block's factor is then incomplete).
+ *              positive (that block's factor is then incomplete), or -1
+ *              when a bounded device wait ran out before the block was
+ *              factored (sympix_plan_status then reports SYMPIX_ETIMEOUT).
  * Asynchronous. */
 int sympix_factor_blocks(sympix_plan_t plan, int storage, int precision, double *blocks, int32_t *info,
                          void *stream);

@@ -68,6 +68,12 @@ def lib():
                                              ctypes.c_double, _dptr, ctypes.c_int, _i32ptr, _i32ptr, _dptr]
         L.sympix_oracle_ordering.restype = ctypes.c_long
         L.sympix_oracle_ordering.argtypes = [ctypes.c_int, ctypes.c_int, _i32ptr, _i64ptr, _i32ptr]
+        L.sympix_oracle_support_margin.restype = ctypes.c_double
+        L.sympix_oracle_support_margin.argtypes = [ctypes.c_int, _dptr, _i32ptr, ctypes.c_double,
+                                                   ctypes.c_int, ctypes.c_int]
+        L.sympix_oracle_guarded_radius.restype = ctypes.c_double
+        L.sympix_oracle_guarded_radius.argtypes = [ctypes.c_int, _dptr, _i32ptr, ctypes.c_double,
+                                                   ctypes.c_int, ctypes.c_int, _dptr]
         _lib = L
     return _lib
 
@@ -172,6 +178,27 @@ def kernel_u(lmax: int, cl: np.ndarray, u) -> np.ndarray:
 
 def pair_u(theta1: float, n1: int, c1: int, theta2: float, n2: int, c2: int) -> float:
     return lib().sympix_oracle_u(float(theta1), int(n1), int(c1), float(theta2), int(n2), int(c2))
+
+
+def support_margin(g: dict, r_s: float, ring0: int = 0, ring1: int | None = None) -> float:
+    """Smallest |u - u_s| / u_s over the pixel pairs of rings [ring0, ring1)."""
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    r1 = g["nrings"] if ring1 is None else int(ring1)
+    return lib().sympix_oracle_support_margin(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), float(r_s),
+                                              int(ring0), r1)
+
+
+def guarded_radius(g: dict, r_s: float, ring0: int = 0, ring1: int | None = None):
+    """(radius, margin): r_s, or r_s scaled by (1 - 1e-9) until no pixel pair
+    lies within 1e-12 (relative) of the support threshold."""
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    r1 = g["nrings"] if ring1 is None else int(ring1)
+    m = ctypes.c_double()
+    r = lib().sympix_oracle_guarded_radius(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), float(r_s),
+                                           int(ring0), r1, ctypes.byref(m))
+    return float(r), float(m.value)
 
 
 def coupled(g: dict, j: int, c: int, rho: int, r_s: float) -> np.ndarray:

@@ -303,6 +303,68 @@ int sympix_oracle_coupled(const double *theta, const int32_t *nring, int j, long
 }
 
 /* ------------------------------------------------------------------------ */
+/* Determinism of the support decision at its threshold                      */
+/* ------------------------------------------------------------------------ */
+
+static long gcd_l(long a, long b)
+{
+    while (b) { long t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* Smallest relative distance |u - u_s| / u_s between the support threshold
+ * u_s = 2 sin^2(r_s / 2) and the u of any pixel pair (c on ring j, p on ring
+ * rho) with j in [ring0, ring1) and rho any ring.  Coupling (u <= u_s) is an
+ * FP64 comparison; two correct implementations (different sin routines) can
+ * only disagree on a pair whose u lies within a few ulps of u_s, so a margin
+ * well above that makes the coupled sets, and every integer derived from
+ * them, implementation-independent.
+ * Pairs: rotating both rings by 2 pi / g, g = gcd(n_j, n_rho), maps pixel c
+ * to c + n_j/g and p to p + n_rho/g and keeps every separation, so columns
+ * c < n_j / g of ring j meet every separation of the ring pair.  A ring whose
+ * nearest possible pair (same longitude, u = 2 sin^2(dtheta/2)) lies above
+ * 2 u_s cannot hold a pair near the threshold and is skipped.
+ * Returns +inf when r_s >= pi (every pair couples, no comparison is made). */
+double sympix_oracle_support_margin(int nrings, const double *theta, const int32_t *nring,
+                                    double r_s, int ring0, int ring1)
+{
+    double us = support_u(r_s);
+    if (!(us < INFINITY)) return INFINITY;
+    double best = INFINITY;
+    for (int j = ring0; j < ring1; ++j) {
+        for (int rho = 0; rho < nrings; ++rho) {
+            double a = sin(0.5 * (theta[j] - theta[rho]));
+            if (2.0 * a * a > 2.0 * us) continue;
+            long g = gcd_l(nring[j], nring[rho]);
+            long P = nring[j] / g;
+            for (long c = 0; c < P; ++c)
+                for (long p = 0; p < nring[rho]; ++p) {
+                    double u = sympix_oracle_u(theta[j], nring[j], c, theta[rho], nring[rho], p);
+                    double m = fabs(u - us) / us;
+                    if (m < best) best = m;
+                }
+        }
+    }
+    return best;
+}
+
+/* The radius both implementations use (reading C5 of the support): r_s
+ * itself when every pair is more than 1e-12 (relative) away from the
+ * threshold, else r_s scaled by (1 - 1e-9), repeatedly, until that holds.
+ * *margin receives the final smallest relative distance. */
+double sympix_oracle_guarded_radius(int nrings, const double *theta, const int32_t *nring,
+                                    double r_s, int ring0, int ring1, double *margin)
+{
+    double m = sympix_oracle_support_margin(nrings, theta, nring, r_s, ring0, ring1);
+    for (int it = 0; it < 8 && m <= 1e-12; ++it) {
+        r_s *= 1.0 - 1e-9;
+        m = sympix_oracle_support_margin(nrings, theta, nring, r_s, ring0, ring1);
+    }
+    if (margin) *margin = m;
+    return r_s;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One preconditioner block (Eq. system-rewritten, Eq. Dhat)                */
 /* ------------------------------------------------------------------------ */
 

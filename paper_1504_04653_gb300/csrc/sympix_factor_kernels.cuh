@@ -296,13 +296,35 @@ constexpr int kF32BandStage = 2 * 17 * 17 * 32;  // floats: two periods of W = 1
 // FUSED: the CTA's warp 0 runs the band pass of the same slice at the same
 // time; this function's NT threads are threads 32 .. 32+NT-1, synchronise
 // among themselves on named barrier 1, stage only rows the band warp has
-// published as final (*prog = periods done), and take the blocks' band-pass
-// results from bandres at the end.
+// published as final (*prog = periods done), meet the band warp on named
+// barrier 2 (all 32+NT threads) at the end, and take the blocks' band-pass
+// results from bandres there.  Each wait for a published period polls at
+// most `limit` times; a wait that runs out sets the CTA's abort flag and
+// the device status bit kStatusTimeout, the sweep stops at the next
+// barrier (every thread reads the flag after the same barrier), waits for
+// its copies in flight, and reports kInfoTimeout for the slice's blocks.
+constexpr int32_t kStatusTimeout = 1;  // bit of the plan's device status word
+constexpr int32_t kInfoTimeout = -1;   // info of a block whose factor a timed-out wait left incomplete
+struct FusedWait {
+    volatile int *prog;    // periods of L11 rows the band warp has published (shared)
+    const int *bandres;    // band-pass result per block (shared)
+    volatile int *abort;   // set when a wait ran out (shared, starts 0)
+    int32_t *status;       // device status word of the plan
+    int limit;             // polls per wait
+};
+
+// Barrier of all 32 + NT threads of the fused kernel (the band warp and the
+// border threads arrive from different code paths, which the non-aligned
+// form allows; every warp arrives as a whole).
+template <int NT>
+__device__ __forceinline__ void fused_barrier_all() {
+    asm volatile("barrier.sync 2, %0;\n" ::"n"(32 + NT) : "memory");
+}
+
 template <int W, int NT, bool FUSED>
 __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
                                            const double *__restrict__ out, const int64_t *s_off, const int *s_n,
-                                           const int *s_live, float *stage, int *binfo, volatile int *prog,
-                                           const int *bandres) {
+                                           const int *s_live, float *stage, int *binfo, const FusedWait *fw) {
     constexpr int RL = W + 1, CH = RL * RL;
     constexpr int NWARP = NT / 32;
     constexpr int R = (W + NWARP - 1) / NWARP;  // border rows per lane
@@ -323,14 +345,22 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     auto issue = [&](int per) {
         const int r0 = per * RL;
         if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
+            bool ready = true;
             if (FUSED) {  // wait until the band warp has finished these rows
                 int spins = 0;
-                while (*prog < per + 1 && ++spins < (1 << 22)) __nanosleep(64);
+                while (*fw->prog < per + 1 && ++spins < fw->limit) __nanosleep(64);
                 __threadfence_block();
+                if (*fw->prog < per + 1) {  // ran out: stop the sweep at the next barrier
+                    ready = false;
+                    *fw->abort = 1;
+                    atomicOr(fw->status, kStatusTimeout);
+                }
             }
-            float *dst = stage + (per % 3) * CH * 32;
-            const float *src = shs + (int64_t)r0 * RL * 32;
-            for (int i = tb; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
+            if (ready) {
+                float *dst = stage + (per % 3) * CH * 32;
+                const float *src = shs + (int64_t)r0 * RL * 32;
+                for (int i = tb; i < CH * 8; i += NT) cp_async16(dst + 4 * i, src + 4 * i);
+            }
         }
         cp_async_commit();
     };
@@ -460,9 +490,14 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     issue(0);
     issue(1);
     const int PW = (kc - 1) / RL;  // the last period
+    bool aborted = false;
     for (int p = 0; p <= PW; ++p) {
         cp_async_wait<1>();  // period p has landed
         bsync();             // ... for every thread's copies; period p-1's buffer is free
+        if (FUSED && *fw->abort) {  // read by every thread after the same barrier
+            aborted = true;
+            break;
+        }
         issue(p + 2);
         if (p > 0) accumulate(vbuf + ((p - 1) & 1) * W * RL * 32);
         vb = vbuf + (p & 1) * W * RL * 32;
@@ -484,7 +519,14 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         }
     }
     cp_async_wait<0>();
-    __syncthreads();  // (fused: the band warp is done too, bandres is final)
+    if (FUSED)
+        fused_barrier_all<NT>();  // the band warp is done too, bandres is final
+    else
+        __syncthreads();
+    if (aborted) {
+        if (tb < 32) binfo[lane] = kInfoTimeout;
+        return;
+    }
     accumulate(vbuf + (PW & 1) * W * RL * 32);
     // the corner: sums to shared memory [block][b][b2], then one thread per
     // block factors C = A22 - S = L22 L22^T in FP64
@@ -494,7 +536,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     for (int i = 0; i < NPC; ++i)
         if (i < npw) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
     bsync();
-    const bool live_end = FUSED ? (live && bandres[lane] == 0) : live;
+    const bool live_end = FUSED ? (live && fw->bandres[lane] == 0) : live;
     if (tb < 32 && live_end) {
         double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
         double *outp = const_cast<double *>(out);
@@ -527,20 +569,18 @@ template <int W, int WMIN, int NT, bool FUSED = false>
 struct F32BorderDispatch {
     __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
                                const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo,
-                               volatile int *prog = nullptr, const int *bandres = nullptr) {
+                               const FusedWait *fw = nullptr) {
         if (w == W) {
-            f32_border<W, NT, FUSED>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog, bandres);
+            f32_border<W, NT, FUSED>(sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, fw);
             return;
         }
-        F32BorderDispatch<W - 1, WMIN, NT, FUSED>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, prog,
-                                                       bandres);
+        F32BorderDispatch<W - 1, WMIN, NT, FUSED>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, fw);
     }
 };
 template <int WMIN, int NT, bool FUSED>
 struct F32BorderDispatch<WMIN - 1, WMIN, NT, FUSED> {
     __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
-                               const int *, const int *, float *, int *, volatile int * = nullptr,
-                               const int * = nullptr) {}
+                               const int *, const int *, float *, int *, const FusedWait * = nullptr) {}
 };
 
 // floats: three staged periods, two periods of L21 values and the last W
@@ -602,6 +642,7 @@ template <class A>
 void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue = 0);
 void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
 void launch_f32_fused(sympix_plan_t pl, int nf, double *blocks, int32_t *info, cudaStream_t st);
+constexpr int kDefaultWaitLimit = 1 << 22;  // polls of a bounded device wait (about 0.3 s)
 void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,
                               cudaStream_t st);
 

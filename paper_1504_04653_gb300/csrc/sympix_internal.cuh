@@ -27,6 +27,10 @@ int cuda_error(cudaError_t e, const char *what);
 // capturing); `name` labels the span since the previous mark, null starts a call.
 void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
 
+// Smallest relative distance |u - u_s| / u_s a support class may have from
+// the coupling threshold before the radius is scaled by (1 - 1e-9).
+constexpr double kSupportMargin = 1e-12;
+
 // Elements of a dense-format block sampled by one CTA (a warp each).
 constexpr int kDenseItemElems = 8;
 
@@ -76,6 +80,7 @@ struct DevBuf {
         if (!v.empty()) SPX_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
         return SYMPIX_OK;
     }
+    size_t bytes() const { return n * sizeof(T); }
     void release() {
         if (p) cudaFree(p);
         p = nullptr;
@@ -160,7 +165,8 @@ struct ConvItem {
 struct sympix_plan_s {
     sympix_grid_t grid = nullptr;
     int nops = 0, ring0 = 0, ring1 = 0;
-    std::vector<double> r_s;
+    std::vector<double> r_s;            // radius used per operator (after the margin guard)
+    std::vector<double> margin;         // smallest |u - u_s| / u_s per operator
     std::vector<int> radius;            // ring offset bound per operator
     std::vector<CanonPair> pairs;       // canonical pairs
     std::vector<int32_t> pair_mmax;     // [pair][op]
@@ -225,4 +231,8 @@ struct sympix_plan_s {
         for (cudaEvent_t e : trace_ev) cudaEventDestroy(e);
     }
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
+    // device status word (bit 1: a bounded wait ran out), read and cleared by
+    // sympix_plan_status; polls per bounded wait (SYMPIX_OPT_WAIT_LIMIT)
+    sympix::DevBuf<int32_t> d_status;
+    int wait_limit = 1 << 22;
 };

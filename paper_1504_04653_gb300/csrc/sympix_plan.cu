@@ -28,10 +28,13 @@ __device__ __forceinline__ double class_u(double base, double st, double denom, 
     return base + st * h * h;
 }
 
-// One thread per (canonical pair, operator): the largest coupled |z|.
+// One thread per (canonical pair, operator): the largest coupled |z|, and
+// the pair's smallest relative distance |u - u_s| / u_s over the classes
+// next to the threshold (the last coupled and the first uncoupled one, or
+// the nearest class when none couples; +inf when r_s >= pi).
 __global__ void k_support_mmax(int npairs, int nops, const CanonPair *__restrict__ pairs,
                                const double *__restrict__ theta, const double *__restrict__ rs,
-                               int32_t *__restrict__ mmax) {
+                               int32_t *__restrict__ mmax, double *__restrict__ margin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npairs * nops) return;
     const int pi = i / nops, o = i % nops;
@@ -43,6 +46,7 @@ __global__ void k_support_mmax(int npairs, int nops, const CanonPair *__restrict
     const double r = rs[o];
     if (r >= kPi) {
         mmax[i] = (int32_t)mcap;
+        margin[i] = INFINITY;
         return;
     }
     const double hs = sin(0.5 * r);
@@ -52,13 +56,25 @@ __global__ void k_support_mmax(int npairs, int nops, const CanonPair *__restrict
     const double base = 2.0 * da * da;
     const double st = 2.0 * sin(ta) * sin(tb);
     const double denom = (double)cp.na * (double)cp.nb;
-    if (class_u(base, st, denom, par * cp.g) > us) {
+    const double u0 = class_u(base, st, denom, par * cp.g);
+    if (u0 > us) {
         mmax[i] = -1;
+        margin[i] = (u0 - us) / us;
         return;
     }
     long m = par;
-    while (m + 2 <= mcap && class_u(base, st, denom, (m + 2) * cp.g) <= us) m += 2;
+    double um = u0, un = INFINITY;
+    while (m + 2 <= mcap) {
+        const double u = class_u(base, st, denom, (m + 2) * cp.g);
+        if (u > us) {
+            un = u;
+            break;
+        }
+        m += 2;
+        um = u;
+    }
     mmax[i] = (int32_t)m;
+    margin[i] = fmin(us - um, un - us) / us;
 }
 
 // One thread per canonical pair: u of each stored class.
@@ -200,21 +216,43 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         }
     const int npairs = (int)pl->pairs.size();
 
-    // device: coupled classes per pair and operator
+    // device: coupled classes per pair and operator.  Coupling is an FP64
+    // comparison u <= u_s; a class whose u lies within 1e-12 (relative) of
+    // u_s could fall either way under another correct sin, so such a radius
+    // is scaled by (1 - 1e-9) until no class is that close (the same rule,
+    // applied the same way, in every implementation of the support).
     int rc;
-    DevBuf<double> d_rs;
+    DevBuf<double> d_rs, d_margin;
     DevBuf<int32_t> d_mmax;
     {
-        std::vector<double> rsv(r_s, r_s + nops);
-        if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = d_rs.upload(rsv)) ||
-            (rc = d_mmax.alloc((size_t)npairs * nops)))
-            return fail(rc);
         const int tot = npairs * nops;
-        k_support_mmax<<<(tot + 127) / 128, 128>>>(npairs, nops, pl->d_pairs.p, grid->d_theta.p, d_rs.p, d_mmax.p);
+        if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = d_mmax.alloc((size_t)tot)) ||
+            (rc = d_margin.alloc((size_t)tot)))
+            return fail(rc);
         pl->pair_mmax.resize((size_t)tot);
-        cudaError_t e = cudaMemcpy(pl->pair_mmax.data(), d_mmax.p, (size_t)tot * sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail(cuda_error(e, "sympix_support: class search"));
+        std::vector<double> marg((size_t)tot);
+        pl->margin.assign(nops, INFINITY);
+        for (int it = 0;; ++it) {
+            if ((rc = d_rs.upload(pl->r_s))) return fail(rc);
+            k_support_mmax<<<(tot + 127) / 128, 128>>>(npairs, nops, pl->d_pairs.p, grid->d_theta.p, d_rs.p,
+                                                       d_mmax.p, d_margin.p);
+            cudaError_t e = cudaMemcpy(pl->pair_mmax.data(), d_mmax.p, (size_t)tot * sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(marg.data(), d_margin.p, (size_t)tot * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return fail(cuda_error(e, "sympix_support: class search"));
+            bool again = false;
+            for (int o = 0; o < nops; ++o) {
+                double mo = INFINITY;
+                for (int pi = 0; pi < npairs; ++pi) mo = std::min(mo, marg[(size_t)pi * nops + o]);
+                pl->margin[o] = mo;
+                if (mo <= kSupportMargin && it < 8) {
+                    pl->r_s[o] *= 1.0 - 1e-9;
+                    again = true;
+                }
+            }
+            if (!again) break;
+        }
     }
     // slots: levels 0..kmax-1 of every canonical pair (max over operators)
     int64_t nslots = 0;
@@ -422,6 +460,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
     for (int l = 0; l < 6; ++l)
         if ((rc = pl->d_factor_items[l].upload(pl->factor_items[l]))) return fail(rc);
+    if ((rc = pl->d_status.alloc(1))) return fail(rc);
+    if (cudaMemset(pl->d_status.p, 0, sizeof(int32_t)) != cudaSuccess)
+        return fail(set_error(SYMPIX_ECUDA, "sympix_support: status word"));
     const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
     const size_t nn = (size_t)nops * grid->npix;
     if ((rc = pl->d_tab_b.alloc(tabn)) || (rc = pl->d_tab_d.alloc(tabn)) || (rc = pl->d_tab_b32.alloc(tabn)) ||
@@ -455,6 +496,12 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         if (value != 256.0 && value != 512.0)
             return set_error(SYMPIX_EINVAL, "sympix_plan_option: border threads are 256 or 512");
         pl->border_threads = (int)value;
+        return SYMPIX_OK;
+    }
+    if (option == SYMPIX_OPT_WAIT_LIMIT) {
+        if (!(value >= 1.0) || value > 2147483647.0 || value != floor(value))
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: wait limit is an integer in [1, 2^31)");
+        pl->wait_limit = (int)value;
         return SYMPIX_OK;
     }
     if (option == SYMPIX_OPT_TRACE) {
@@ -642,6 +689,41 @@ extern "C" int sympix_block_layout(sympix_plan_t pl, int storage, int op, int ri
     if (n) *n = bd.n;
     if (w) *w = bd.w;
     if (format) *format = pb ? bd.format : SYMPIX_BLOCK_DENSE;
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_plan_status(sympix_plan_t pl, void *stream) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_status: NULL plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t v = 0;
+    SPX_CUDA(cudaMemcpyAsync(&v, pl->d_status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SPX_CUDA(cudaMemsetAsync(pl->d_status.p, 0, sizeof(int32_t), st));
+    SPX_CUDA(cudaStreamSynchronize(st));
+    if (v & 1) return set_error(SYMPIX_ETIMEOUT, "a bounded device wait of the factorisation ran out");
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_plan_radius(sympix_plan_t pl, int op, double *r_s, double *margin) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_radius: NULL plan");
+    if (op < 0 || op >= pl->nops) return set_error(SYMPIX_EINVAL, "sympix_plan_radius: op %d not planned", op);
+    if (r_s) *r_s = pl->r_s[op];
+    if (margin) *margin = pl->margin[op];
+    return SYMPIX_OK;
+}
+
+extern "C" int sympix_plan_device_bytes(sympix_plan_t pl, size_t *bytes, size_t *staging) {
+    if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_device_bytes: NULL plan");
+    size_t b = pl->d_pairs.bytes() + pl->d_slot_u.bytes() + pl->d_slot_pair.bytes() + pl->d_tab_b.bytes() +
+               pl->d_tab_d.bytes() + pl->d_tab_b32.bytes() + pl->d_tab_blo.bytes() + pl->d_tab_d32.bytes() +
+               pl->d_tab_dlo.bytes() + pl->d_ninv32.bytes() + pl->d_ninvlo.bytes() + pl->d_rec.bytes() +
+               pl->d_blocks.bytes() + pl->d_entries.bytes() + pl->d_items_dense.bytes() +
+               pl->d_items_dense_rows.bytes() + pl->d_items_conv.bytes() + pl->d_f32_items.bytes() +
+               pl->d_f32_slices.bytes() + pl->d_f32_tiles.bytes() + pl->d_shadow_il.bytes() +
+               pl->d_l21_il.bytes() + pl->d_f32_out_tiles.bytes() + pl->d_shadow.bytes();
+    for (int i = 0; i < 5; ++i) b += pl->d_items_pband[i].bytes();
+    for (int i = 0; i < 6; ++i) b += pl->d_factor_items[i].bytes();
+    if (bytes) *bytes = b;
+    if (staging) *staging = pl->d_rec.bytes();
     return SYMPIX_OK;
 }
 

@@ -121,24 +121,19 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
     }
 }
 
-}  // namespace sympix
-
-using namespace sympix;
-
-extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const double *dl, void *stream) {
-    if (!pl || !bl || !dl) return set_error(SYMPIX_EINVAL, "sympix_kernel_table: NULL argument");
-    cudaStream_t st = (cudaStream_t)stream;
+// The launches of one kernel-table call with the coefficient staging at
+// `rec` (2 (lmax+1) (nops+1) doubles): the coefficients, then the table in
+// chunks of 8, 4, 2 or 1 operators sharing one recurrence, with a trace
+// mark after each.  Both entry points run exactly this sequence.
+static int launch_table(sympix_plan_t pl, const double *bl, const double *dl, double *rec, cudaStream_t st,
+                        const char *who) {
     const int lmax = pl->grid->lmax;
-    const int L1 = lmax + 1;
-    int rc;
-    if (pl->d_rec.n < (size_t)(2 * L1 + 2 * pl->nops * L1)) {
-        if ((rc = pl->d_rec.alloc((size_t)(2 * L1 + 2 * pl->nops * L1)))) return rc;
-    }
-    double *rec = pl->d_rec.p;
+    const size_t L1 = (size_t)lmax + 1;
     double *cb = rec + 2 * L1;
     double *cd = cb + (size_t)pl->nops * L1;
-    const int tot = pl->nops * L1;
+    const int tot = pl->nops * (int)L1;
     trace_mark(pl, st, nullptr);
+    // every staging entry read below is written first by k_table_coeffs
     k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
     trace_mark(pl, st, "k_table_coeffs");
     if (pl->nslots > 0) {
@@ -165,9 +160,24 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
     }
     trace_mark(pl, st, "k_table");
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table: launch");
+    if (e != cudaSuccess) return cuda_error(e, who);
     pl->table_ready = true;
     return SYMPIX_OK;
+}
+
+}  // namespace sympix
+
+using namespace sympix;
+
+extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const double *dl, void *stream) {
+    if (!pl || !bl || !dl) return set_error(SYMPIX_EINVAL, "sympix_kernel_table: NULL argument");
+    const size_t L1 = (size_t)pl->grid->lmax + 1;
+    const size_t need = 2 * L1 + 2 * (size_t)pl->nops * L1;
+    int rc;
+    if (pl->d_rec.n < need) {
+        if ((rc = pl->d_rec.alloc(need))) return rc;
+    }
+    return launch_table(pl, bl, dl, pl->d_rec.p, (cudaStream_t)stream, "sympix_kernel_table: launch");
 }
 
 extern "C" int sympix_table_copy(sympix_plan_t pl, int op, int ring, int rho, int count, double *b, double *d) {
@@ -237,35 +247,5 @@ extern "C" int sympix_kernel_table_static(sympix_plan_t pl, const double *bl, co
         }
         scratch = addr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    double *rec = scratch;
-    double *cb = rec + 2 * L1;
-    double *cd = cb + (size_t)pl->nops * L1;
-    const int tot = pl->nops * (int)L1;
-    // every scratch entry read below is written first by k_table_coeffs
-    k_table_coeffs<<<(tot + 255) / 256, 256, 0, st>>>(lmax, pl->nops, bl, dl, rec, cb, cd);
-    if (pl->nslots > 0) {
-        const int cta = pl->table_cta;
-        const unsigned grid = (unsigned)((pl->nslots + cta * kTableSpt - 1) / (cta * kTableSpt));
-        for (int op0 = 0; op0 < pl->nops;) {
-            const int left = pl->nops - op0;
-            const int chunk = left >= 4 ? 4 : left >= 2 ? 2 : 1;
-#define SPX_TABLE_S(NO)                                                                                            \
-    k_table<NO><<<grid, cta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
-                                      pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
-                                      pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
-            if (chunk == 4)
-                SPX_TABLE_S(4);
-            else if (chunk == 2)
-                SPX_TABLE_S(2);
-            else
-                SPX_TABLE_S(1);
-#undef SPX_TABLE_S
-            op0 += chunk;
-        }
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "sympix_kernel_table_static: launch");
-    pl->table_ready = true;
-    return SYMPIX_OK;
+    return launch_table(pl, bl, dl, scratch, (cudaStream_t)stream, "sympix_kernel_table_static: launch");
 }

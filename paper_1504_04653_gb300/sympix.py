@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
-OPT_FP32_PIVOT_FLOOR, OPT_TRACE, OPT_TABLE_CTA, OPT_BORDER_THREADS = 1, 2, 3, 4
+OPT_FP32_PIVOT_FLOOR, OPT_TRACE, OPT_TABLE_CTA, OPT_BORDER_THREADS, OPT_WAIT_LIMIT = 1, 2, 3, 4, 5
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
@@ -60,6 +60,9 @@ SIGNATURES = [
     ("sympix_blocks_size", _i, [_vp, _i, _sizep, _i64p]),
     ("sympix_block_layout", _i, [_vp, _i, _i, _i, _i64p, _i32p, _i32p, _i32p]),
     ("sympix_support_copy", _i, [_vp, _i, _i, _i, _i32p]),
+    ("sympix_plan_radius", _i, [_vp, _i, _dp, _dp]),
+    ("sympix_plan_status", _i, [_vp, _vp]),
+    ("sympix_plan_device_bytes", _i, [_vp, _sizep, _sizep]),
     ("sympix_kernel_table", _i, [_vp, _vp, _vp, _vp]),
     ("sympix_kernel_table_static", _i, [_vp, _vp, _vp, _vp]),
     ("sympix_table_copy", _i, [_vp, _i, _i, _i, _i, _dp, _dp]),
@@ -216,6 +219,14 @@ class Plan:
                                      _ptr(info), _stream(stream)))
         return self.tuning()
 
+    def set_wait_limit(self, polls: int):
+        """Polls of a bounded device wait (the FP32 factor's border warps)."""
+        _check(lib().sympix_plan_option(self._h, OPT_WAIT_LIMIT, float(polls)))
+
+    def status(self, stream=None):
+        """Raise SympixError(ETIMEOUT) if a bounded device wait ran out since the last call."""
+        _check(lib().sympix_plan_status(self._h, _stream(stream)))
+
     def set_trace(self, on: bool):
         """Record a CUDA event after every kernel launch of direct calls."""
         _check(lib().sympix_plan_option(self._h, OPT_TRACE, 1.0 if on else 0.0))
@@ -236,6 +247,18 @@ class Plan:
                                           PRECISIONS[factor_precision], ctypes.byref(a), ctypes.byref(b),
                                           ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def radius(self, op=0):
+        """(support radius used, smallest relative margin |u - u_s| / u_s)."""
+        r, m = ctypes.c_double(), ctypes.c_double()
+        _check(lib().sympix_plan_radius(self._h, int(op), ctypes.byref(r), ctypes.byref(m)))
+        return r.value, m.value
+
+    def device_bytes(self):
+        """(device bytes the plan holds, of which the table's coefficient staging)."""
+        b, st = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().sympix_plan_device_bytes(self._h, ctypes.byref(b), ctypes.byref(st)))
+        return b.value, st.value
 
     def support(self, op, ring, radius):
         out = np.zeros(2 * radius + 1, np.int32)

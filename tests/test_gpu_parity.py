@@ -89,17 +89,15 @@ def test_dp_grid_matches_oracle(S, lmax, k, thr):
 # -- support and kernel table ---------------------------------------------------------
 
 def _coupled_from_mmax(n_j, n_rho, c, m):
+    """Columns p of ring rho coupled to column c of ring j by the rule
+    |z| <= m, z = (2c+1) Q - (2p+1) P reduced to the nearest longitude."""
     g = math.gcd(n_j, n_rho)
     P, Q = n_j // g, n_rho // g
     half = P * n_rho
-    out = []
-    for p in range(n_rho):
-        z = ((2 * c + 1) * Q - (2 * p + 1) * P) % (2 * half)
-        if z > half:
-            z -= 2 * half
-        if abs(z) <= m:
-            out.append(p)
-    return np.array(out, dtype=np.int32)
+    p = np.arange(n_rho, dtype=np.int64)
+    z = ((2 * c + 1) * Q - (2 * p + 1) * P) % (2 * half)
+    z = np.where(z > half, z - 2 * half, z)
+    return p[np.abs(z) <= m].astype(np.int32)
 
 
 @pytest.mark.parametrize("name,rings", [("lmax64", None), ("lmax500", [0, 1, 2, 3, 60, 249, 250, 251, 498, 500])])
@@ -122,6 +120,88 @@ def test_support_matches_oracle_bruteforce(S, name, rings):
                 ref = O.coupled(og, j, c, rho, r_s)
                 got = _coupled_from_mmax(n_j, n_r, c, mm[d + R]) if mm[d + R] >= 0 else np.zeros(0, np.int32)
                 assert np.array_equal(got, ref), (j, rho, c)
+
+
+def test_support_every_ring_lmax3000(S):
+    """l_max = 3000, FWHM 5': the coupled pixel sets of every ring and every
+    neighbour ring, at three columns each, bit for bit against the oracle's
+    direct test of every pixel pair."""
+    wl = W.WORKLOADS["lmax3000"]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    og = O.grid(wl.lmax)
+    r_s = plan.radius(0)[0]
+    N, R = grid.nrings, 6  # r_s is about 4 ring spacings
+    checked = 0
+    for j in range(N):
+        mm = plan.support(0, j, R)
+        n_j = int(grid.nring[j])
+        for d in range(-R, R + 1):
+            rho = j + d
+            if rho < 0 or rho >= N:
+                continue
+            n_r = int(grid.nring[rho])
+            for c in sorted({0, n_j // 3, n_j - 1}):
+                ref = O.coupled(og, j, c, rho, r_s)
+                got = _coupled_from_mmax(n_j, n_r, c, mm[d + R]) if mm[d + R] >= 0 else np.zeros(0, np.int32)
+                assert np.array_equal(got, ref), (j, rho, c)
+                checked += len(ref)
+    assert checked > 10 * N
+
+
+def _golden_margins():
+    from pathlib import Path
+    rows = []
+    path = Path(__file__).resolve().parent / "golden" / "support_margins.txt"
+    for line in path.read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            name, op, lmax, r_s, r_used, margin = line.split()
+            rows.append((name, int(op), int(lmax), float.fromhex(r_s), float.fromhex(r_used), float(margin)))
+    return rows
+
+
+@pytest.mark.parametrize("name", ["lmax64", "lmax500", "lmax1500", "lmax3000", "batched32"])
+def test_support_radius_and_margin_match_oracle(S, name):
+    """The plan's threshold guard takes the oracle's decision at every
+    measured workload: the same radius (bit for bit) and the same smallest
+    distance of any class from the threshold."""
+    wl = W.WORKLOADS[name]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    rows = [r for r in _golden_margins() if r[0] == name]
+    assert len(rows) == wl.nops
+    for _, op, _, r_s, r_used, margin in rows:
+        assert wl.radii()[op] == r_s
+        r, m = plan.radius(op)
+        assert r == r_used, (name, op)
+        assert abs(m - margin) <= 1e-6 * margin, (name, op, m, margin)
+
+
+def test_support_guard_moves_a_radius_off_a_class(S):
+    """A radius placed exactly on one pixel pair's separation: the plan
+    scales it as the oracle does, and the coupled sets follow the scaled
+    radius on both sides."""
+    grid = S.Grid(32)
+    og = O.grid(32)
+    j, rho = 10, 12
+    u = O.pair_u(og["theta"][j], og["nring"][j], 0, og["theta"][rho], og["nring"][rho], 1)
+    r_on = 2.0 * math.asin(math.sqrt(u / 2.0))
+    r_ref, m_ref = O.guarded_radius(og, r_on)
+    assert r_ref != r_on
+    plan = S.Plan(grid, np.array([r_on]))
+    r, m = plan.radius(0)
+    assert r == r_ref and m > 1e-12
+    R = 6
+    for jj in (j, rho):
+        mm = plan.support(0, jj, R)
+        for d in range(-R, R + 1):
+            rr = jj + d
+            if mm[d + R] < 0:
+                continue
+            for c in range(int(grid.nring[jj])):
+                ref = O.coupled(og, jj, c, rr, r_ref)
+                got = _coupled_from_mmax(int(grid.nring[jj]), int(grid.nring[rr]), c, mm[d + R])
+                assert np.array_equal(got, ref), (jj, rr, c)
 
 
 @pytest.mark.parametrize("name", ["lmax64", "lmax500", "lmax3000"])
@@ -298,18 +378,31 @@ def test_indefinite_block_reports_pivot(S, dev):
 
 # -- full size, in the bench's configuration ----------------------------------------------
 
+_ORACLE_3000 = {}
+
+
+def _oracle_block_3000(j, ninv0):
+    """The oracle's block of ring j at l_max = 3000 (kept for the module:
+    the equatorial ring takes the oracle tens of seconds)."""
+    if j not in _ORACLE_3000:
+        wl = W.WORKLOADS["lmax3000"]
+        og = _ORACLE_3000.setdefault("grid", O.grid(wl.lmax))
+        _ORACLE_3000[j] = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv0, j)[0]
+    return _ORACLE_3000[j]
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp32x2", "fp64"])
 def test_full_size_lmax3000_sampled(S, dev, precision):
     """l_max = 3000, FWHM 5': every block factors; sampled blocks match the
-    oracle and their factors reproduce them."""
+    oracle and their factors reproduce them, from the pole to the equator
+    (ring 1500, 6075 pixels, the longest elimination chain)."""
     wl = W.WORKLOADS["lmax3000"]
     r = _run(S, dev, wl, precision=precision, factor=True)
     assert np.all(r["info"] == 0)
-    og = O.grid(wl.lmax)
     plan = r["plan"]
-    for j in (0, 2, 37, 1500 if precision == "fp32" else 250):
+    for j in (0, 2, 37, 250, 1500):
         M = S.unpack_block(r["sampled"], plan, "pband", 0, j)
-        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], r["ninv"][0], j)
+        ref = _oracle_block_3000(j, r["ninv"][0])
         assert _err(M, ref) <= TOL[precision], (j, _err(M, ref))
         L = S.unpack_block(r["factored"], plan, "pband", 0, j, factored=True)
         assert _err(L @ L.T, ref) <= 10 * TOL[precision], j
@@ -529,18 +622,21 @@ def _dense_block(sampled, plan, storage, ring):
 
 
 def test_dense_storage_large_blocks_lmax1500(S, dev):
-    """Dense storage at l_max = 1500 (rings of ~3000 pixels): L L^T
-    reproduces the sampled block to FP64 accuracy."""
+    """Dense storage at l_max = 1500 (rings of ~3000 pixels): the sampled
+    blocks match the oracle's and L L^T reproduces them to FP64 accuracy."""
     wl = W.WORKLOADS["lmax1500"]
     grid = S.Grid(wl.lmax)
     j0 = grid.nrings // 2 - 1
     r = _run(S, dev, wl, grid=grid, ring0=j0, ring1=j0 + 2, precision="fp64", storage="dense", factor=True)
     assert np.all(r["info"] == 0)
+    og = O.grid(wl.lmax)
     for j in (j0, j0 + 1):
         M, _, n = _dense_block(r["sampled"], r["plan"], "dense", j)
         L = np.tril(_dense_block(r["factored"], r["plan"], "dense", j)[0])
         assert n > 1024
-        assert _err(L @ L.T, np.tril(M) + np.tril(M, -1).T) <= 1e-11
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], r["ninv"][0], j)
+        assert _err(M, ref) <= TOL["fp64"], (j, _err(M, ref))
+        assert _err(L @ L.T, ref) <= 1e-11
 
 
 def test_pband_storage_dense_format_large_blocks(S, dev):

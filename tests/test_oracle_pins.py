@@ -470,3 +470,104 @@ def test_convolve_truncated_matches_brute_force():
     out, pairs = O.convolve(g, bl, r_s, f, ring, col)
     assert pairs == int((np.arccos(x) <= r_s).sum())
     assert np.allclose(out, want, rtol=1e-10, atol=1e-12 * np.abs(want).max())
+
+
+# -- truncated blocks: dense brute force (Eq. Dhat, Eq. f truncation) ------------
+
+def _unit_vectors(g):
+    th, ph, _, _ = _pixel_angles(g)
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+
+
+def _truncated_dense(g, coef_l, r_s):
+    """Every pixel pair of the grid: x = n_p . n_q from 3-vectors, the kernel
+    by numpy's Legendre series sum (2l+1)/(4 pi) c_l P_l(x), zero where the
+    angle arccos(x) exceeds r_s."""
+    from numpy.polynomial import legendre as Lg
+    v = _unit_vectors(g)
+    x = np.clip(v @ v.T, -1.0, 1.0)
+    lmax = len(coef_l) - 1
+    series = (2 * np.arange(lmax + 1) + 1) / (4 * np.pi) * coef_l
+    return np.where(np.arccos(x) <= r_s, Lg.legval(x, series), 0.0), x
+
+
+@pytest.mark.parametrize("lmax,radii", [(12, (0.31, 0.77)), (16, (0.23, 0.52))])
+def test_truncated_block_matches_dense_brute_force(lmax, radii):
+    """With a support radius below pi every ring block of the oracle equals
+    the ring's diagonal block of the dense product D^ + B^T diag(N^-1) B^,
+    built here from 3-vector dot products, numpy's Legendre series and
+    arccos masks, with N^-1 holding masked zeros."""
+    g = O.grid(lmax)
+    rng = np.random.default_rng(lmax + 100)
+    bl = np.exp(-0.015 * np.arange(lmax + 1) * (np.arange(lmax + 1) + 1))
+    dl = rng.uniform(0.2, 1.0, lmax + 1)
+    th, _, _, _ = _pixel_angles(g)
+    ninv = rng.uniform(0.5, 2.0, g["npix"])
+    ninv[np.abs(0.5 * np.pi - th) < 0.3] = 0.0  # a masked band
+    assert np.any(ninv == 0.0)
+    for r_s in radii:
+        B, x = _truncated_dense(g, bl, r_s)
+        D, _ = _truncated_dense(g, dl, r_s)
+        # no pair sits on the threshold, so the two masks cannot differ
+        gam = np.arccos(x)
+        assert np.min(np.abs(gam - r_s)) > 1e-9
+        assert 0 < np.count_nonzero(B) < B.size  # truncated, not empty
+        full = D + B.T @ (ninv[:, None] * B)
+        for j in range(g["nrings"]):
+            M, _ = O.block(g, bl, dl, r_s, ninv, j)
+            n = g["nring"][j]
+            idx = g["ring_offset"][j] + g["ring_stride"][j] * np.arange(n)
+            ref = full[np.ix_(idx, idx)]
+            assert np.max(np.abs(M - ref)) <= 1e-12 * np.max(np.abs(ref)), (r_s, j)
+
+
+def test_support_margin_matches_brute_force():
+    """The smallest |u - u_s| / u_s over all pixel pairs, from 3-vectors."""
+    g = O.grid(16)
+    v = _unit_vectors(g)
+    u_all = 1.0 - v @ v.T
+    for r_s in (0.23, 0.52, 1.1):
+        us = 2 * math.sin(r_s / 2) ** 2
+        ref = np.min(np.abs(u_all - us)) / us
+        got = O.support_margin(g, r_s)
+        assert abs(got - ref) <= 1e-6 * ref + 1e-13, (r_s, got, ref)
+    assert O.support_margin(g, math.pi) == math.inf
+
+
+def test_guard_moves_a_radius_off_a_class():
+    """A radius placed exactly on the separation of a pixel pair has margin
+    ~0; the guard scales it by (1 - 1e-9) until every class is > 1e-12
+    away, and leaves a radius with a comfortable margin alone."""
+    g = O.grid(32)
+    j, rho = 10, 12
+    u = O.pair_u(g["theta"][j], g["nring"][j], 0, g["theta"][rho], g["nring"][rho], 1)
+    r_on = 2.0 * math.asin(math.sqrt(u / 2.0))
+    assert O.support_margin(g, r_on) <= 1e-12
+    r, m = O.guarded_radius(g, r_on)
+    assert r == r_on * (1.0 - 1e-9) and m > 1e-12
+    # the guarded radius no longer couples that pair
+    assert 1 not in O.coupled(g, j, 0, rho, r)
+    r2, m2 = O.guarded_radius(g, 0.2)
+    assert r2 == 0.2 and m2 > 1e-12
+
+
+def _golden_margins():
+    rows = []
+    for line in (GOLDEN / "support_margins.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        name, op, lmax, r_s, r_used, margin = line.split()
+        rows.append((name, int(op), int(lmax), float.fromhex(r_s), float.fromhex(r_used), float(margin)))
+    return rows
+
+
+def test_golden_margins_reproduce():
+    """The stored margins (written by tests/golden/make_support_margins.py,
+    which calls the oracle only) are the oracle's, for the cheap workloads."""
+    rows = [r for r in _golden_margins() if r[2] <= 500]
+    assert rows
+    for name, op, lmax, r_s, r_used, margin in rows:
+        r, m = O.guarded_radius(O.grid(lmax), r_s)
+        assert r == r_used and abs(m - margin) <= 1e-6 * margin, name
+    # every measured workload keeps its radius: no class is near the threshold
+    assert all(r[3] == r[4] and r[5] > 1e-9 for r in _golden_margins())

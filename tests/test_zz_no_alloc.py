@@ -100,3 +100,49 @@ def test_static_table_rejects_oversize(S):
                                             ctypes.c_void_p(bl.data_ptr()), None)
     assert rc == S.EINVAL
     assert b"static array" in S.lib().sympix_last_error()
+
+
+def test_static_table_on_a_fresh_plan_allocates_nothing(S):
+    """On a plan that has never had a table, the allocation-free call leaves
+    the plan's device memory as it was (no staging buffer appears), and its
+    tables equal those of the regular entry point, which allocates its
+    staging on this first use.  Nine operators: a chunk of eight sharing one
+    recurrence, then one, in both entry points."""
+    import torch
+    dev = torch.device("cuda", 0)
+    nops = 9
+    fwhm = [180.0 + 15.0 * o for o in range(nops)]
+    wl = W.Workload("nine", 64, fwhm, [0.0] * nops, list(range(nops)))
+    grid = S.Grid(wl.lmax)
+    bl = torch.tensor(wl.beams(), dtype=torch.float64, device=dev)
+    dl = torch.tensor(wl.priors(), dtype=torch.float64, device=dev)
+    lib = S.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    fresh = S.Plan(grid, wl.radii())
+    total0, staging0 = fresh.device_bytes()
+    assert staging0 == 0
+    rc = lib.sympix_kernel_table_static(fresh.handle, ctypes.c_void_p(bl.data_ptr()),
+                                        ctypes.c_void_p(dl.data_ptr()), stream)
+    assert rc == 0, lib.sympix_last_error()
+    torch.cuda.synchronize()
+    assert fresh.device_bytes() == (total0, 0)
+
+    regular = S.Plan(grid, wl.radii())
+    S.sympix_kernel_table(regular, bl, dl)
+    torch.cuda.synchronize()
+    assert regular.device_bytes()[1] == 2 * (wl.lmax + 1) * (nops + 1) * 8
+    R = 10
+    for o in range(nops):
+        for j in range(grid.nrings):
+            mm = regular.support(o, j, R)
+            assert np.array_equal(mm, fresh.support(o, j, R))
+            for d in range(-R, R + 1):
+                if mm[d + R] < 0:
+                    continue
+                K = mm[d + R] // 2 + 1
+                got = fresh.table(o, j, j + d, K)
+                ref = regular.table(o, j, j + d, K)
+                assert np.array_equal(got[0], ref[0]), (o, j, d)
+                if ref[1] is not None:
+                    assert np.array_equal(got[1], ref[1]), (o, j, d)
