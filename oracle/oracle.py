@@ -68,6 +68,11 @@ def lib():
                                              ctypes.c_double, _dptr, ctypes.c_int, _i32ptr, _i32ptr, _dptr]
         L.sympix_oracle_ordering.restype = ctypes.c_long
         L.sympix_oracle_ordering.argtypes = [ctypes.c_int, ctypes.c_int, _i32ptr, _i64ptr, _i32ptr]
+        L.sympix_oracle_block_pair.restype = ctypes.c_long
+        L.sympix_oracle_block_pair.argtypes = [ctypes.c_int, _dptr, _i32ptr, _i64ptr, _i32ptr,
+                                               ctypes.c_int, _dptr, _dptr, ctypes.c_double,
+                                               _dptr, ctypes.c_int, ctypes.c_int, _dptr]
+        L.sympix_oracle_trisolve.argtypes = [ctypes.c_int, _dptr, _dptr, ctypes.c_int, _dptr]
         L.sympix_oracle_support_margin.restype = ctypes.c_double
         L.sympix_oracle_support_margin.argtypes = [ctypes.c_int, _dptr, _i32ptr, ctypes.c_double,
                                                    ctypes.c_int, ctypes.c_int]
@@ -229,6 +234,35 @@ def block(g: dict, bl: np.ndarray, dl: np.ndarray, r_s: float, ninv: np.ndarray,
                                         _p(b, _dptr), _p(d, _dptr), float(r_s),
                                         _p(nv, _dptr), int(j), _p(M, _dptr))
     return M, int(triples)
+
+
+def block_pair(g: dict, bl: np.ndarray, dl: np.ndarray, r_s: float, ninv: np.ndarray, j: int, k: int):
+    """Dense block between ring j (rows) and ring k (columns), and the triples summed."""
+    nj, nk = int(g["nring"][j]), int(g["nring"][k])
+    M = np.zeros((nj, nk), dtype=np.float64)
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    off = np.ascontiguousarray(g["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g["ring_stride"], dtype=np.int32)
+    b = _f64(bl)
+    d = _f64(dl)
+    nv = _f64(ninv)
+    assert len(nv) == g["npix"]
+    triples = lib().sympix_oracle_block_pair(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), _p(off, _i64ptr),
+                                             _p(st, _i32ptr), g["lmax"], _p(b, _dptr), _p(d, _dptr), float(r_s),
+                                             _p(nv, _dptr), int(j), int(k), _p(M, _dptr))
+    return M, int(triples)
+
+
+def trisolve(L: np.ndarray, b: np.ndarray, trans: bool = False) -> np.ndarray:
+    """Solve L y = b (or L^T y = b) by substitution."""
+    L = _f64(L)
+    bb = _f64(b)
+    y = np.zeros_like(bb)
+    rc = lib().sympix_oracle_trisolve(L.shape[0], _p(L, _dptr), _p(bb, _dptr), 1 if trans else 0, _p(y, _dptr))
+    if rc != 0:
+        raise ValueError(f"zero diagonal at row {rc - 1}")
+    return y
 
 
 def convolve(g: dict, bl: np.ndarray, r_s: float, f: np.ndarray, q_ring, q_col):

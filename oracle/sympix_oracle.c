@@ -422,6 +422,98 @@ long sympix_oracle_block(int nrings, const double *theta, const int32_t *nring,
     return triples;
 }
 
+/* The block of the same operator between two rings (Eq. system-rewritten,
+ * Eq. Dhat), dense n_j x n_k, row-major, rows on ring j and columns on ring
+ * k:
+ *   M_qr = [u_qr <= u_s] d(1-u_qr)
+ *        + sum over pixels p of every ring with u_pq <= u_s and u_pr <= u_s of
+ *          b(1-u_pq) N^-1_p b(1-u_pr).
+ * With k = j this is sympix_oracle_block.  Summed p by p as there: for each
+ * p the coupled pixels of both rings are listed with their kernel values and
+ * every (q, r) pair of them receives its product.  Returns the triples. */
+long sympix_oracle_block_pair(int nrings, const double *theta, const int32_t *nring,
+                              const int64_t *ring_offset, const int32_t *ring_stride,
+                              int lmax, const double *bl, const double *dl, double r_s,
+                              const double *ninv, int j, int k, double *M)
+{
+    int nj = nring[j], nk = nring[k];
+    double us = support_u(r_s);
+    memset(M, 0, sizeof(double) * (size_t)nj * nk);
+
+    /* D^ between the two rings */
+    for (long q = 0; q < nj; ++q)
+        for (long r = 0; r < nk; ++r) {
+            double u = sympix_oracle_u(theta[j], nj, q, theta[k], nk, r);
+            if (u <= us) M[q * nk + r] += sympix_oracle_kernel_u(lmax, dl, u);
+        }
+
+    /* B^T N^-1 B^, summed over every pixel p of every ring */
+    long triples = 0;
+    int32_t *iq = (int32_t *)malloc(sizeof(int32_t) * nj);
+    int32_t *ir = (int32_t *)malloc(sizeof(int32_t) * nk);
+    double *vq = (double *)malloc(sizeof(double) * nj);
+    double *vr = (double *)malloc(sizeof(double) * nk);
+    for (int rho = 0; rho < nrings; ++rho) {
+        double a1 = sin(0.5 * (theta[j] - theta[rho]));
+        double a2 = sin(0.5 * (theta[k] - theta[rho]));
+        if (2.0 * a1 * a1 > us || 2.0 * a2 * a2 > us) continue; /* no pixel of rho reaches both */
+        for (long p = 0; p < nring[rho]; ++p) {
+            int cq = 0, cr = 0;
+            for (long q = 0; q < nj; ++q) {
+                double u = sympix_oracle_u(theta[j], nj, q, theta[rho], nring[rho], p);
+                if (u <= us) {
+                    iq[cq] = (int32_t)q;
+                    vq[cq] = sympix_oracle_kernel_u(lmax, bl, u);
+                    ++cq;
+                }
+            }
+            if (!cq) continue;
+            for (long r = 0; r < nk; ++r) {
+                double u = sympix_oracle_u(theta[k], nk, r, theta[rho], nring[rho], p);
+                if (u <= us) {
+                    ir[cr] = (int32_t)r;
+                    vr[cr] = sympix_oracle_kernel_u(lmax, bl, u);
+                    ++cr;
+                }
+            }
+            double np = ninv[ring_offset[rho] + p * (int64_t)ring_stride[rho]];
+            for (int x = 0; x < cq; ++x)
+                for (int y = 0; y < cr; ++y)
+                    M[(size_t)iq[x] * nk + ir[y]] += vq[x] * np * vr[y];
+            triples += (long)cq * cr;
+        }
+    }
+    free(iq); free(ir); free(vq); free(vr);
+    return triples;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangular solves with a Cholesky factor (applying M^-1 = L^-T L^-1)      */
+/* ------------------------------------------------------------------------ */
+
+/* Solve L y = b (trans = 0, forward substitution) or L^T y = b (trans = 1,
+ * back substitution) for a lower-triangular n x n row-major L.  Returns 0, or
+ * i+1 for the first zero diagonal met. */
+int sympix_oracle_trisolve(int n, const double *L, const double *b, int trans, double *y)
+{
+    if (!trans) {
+        for (int i = 0; i < n; ++i) {
+            double s = b[i];
+            for (int c = 0; c < i; ++c) s -= L[(size_t)i * n + c] * y[c];
+            if (L[(size_t)i * n + i] == 0.0) return i + 1;
+            y[i] = s / L[(size_t)i * n + i];
+        }
+    } else {
+        for (int i = n - 1; i >= 0; --i) {
+            double s = b[i];
+            for (int c = i + 1; c < n; ++c) s -= L[(size_t)c * n + i] * y[c];
+            if (L[(size_t)i * n + i] == 0.0) return i + 1;
+            y[i] = s / L[(size_t)i * n + i];
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Pixel-domain convolution (Eq. convolution-pixel)                          */
 /* ------------------------------------------------------------------------ */

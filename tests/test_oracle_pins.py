@@ -571,3 +571,66 @@ def test_golden_margins_reproduce():
         assert r == r_used and abs(m - margin) <= 1e-6 * margin, name
     # every measured workload keeps its radius: no class is near the threshold
     assert all(r[3] == r[4] and r[5] > 1e-9 for r in _golden_margins())
+
+
+# -- blocks between two rings and triangular solves (applying M^-1) --------------
+
+@pytest.mark.parametrize("lmax,r_s", [(12, 0.52), (16, 0.31)])
+def test_block_pair_matches_dense_brute_force(lmax, r_s):
+    """Blocks between rings j and k (k = j, j +- 1, j +- 2, and a ring out of
+    reach) equal the corresponding sub-block of the dense truncated
+    D^ + B^T diag(N^-1) B^ from 3-vectors, numpy's Legendre series and arccos
+    masks."""
+    g = O.grid(lmax)
+    rng = np.random.default_rng(lmax + 200)
+    bl = np.exp(-0.02 * np.arange(lmax + 1) * (np.arange(lmax + 1) + 1))
+    dl = rng.uniform(0.2, 1.0, lmax + 1)
+    th, _, _, _ = _pixel_angles(g)
+    ninv = rng.uniform(0.5, 2.0, g["npix"])
+    ninv[np.abs(0.5 * np.pi - th) < 0.25] = 0.0
+    B, x = _truncated_dense(g, bl, r_s)
+    D, _ = _truncated_dense(g, dl, r_s)
+    assert np.min(np.abs(np.arccos(x) - r_s)) > 1e-9
+    full = D + B.T @ (ninv[:, None] * B)
+    N = g["nrings"]
+    idx = [g["ring_offset"][j] + g["ring_stride"][j] * np.arange(g["nring"][j]) for j in range(N)]
+    for j, k in [(3, 3), (3, 4), (4, 3), (5, 7), (N // 2, N // 2 + 1), (N - 1, N - 2), (0, N - 1)]:
+        M, _ = O.block_pair(g, bl, dl, r_s, ninv, j, k)
+        ref = full[np.ix_(idx[j], idx[k])]
+        scale = max(np.max(np.abs(full[np.ix_(idx[j], idx[j])])), 1e-300)
+        assert np.max(np.abs(M - ref)) <= 1e-12 * scale, (j, k)
+    M0, t0 = O.block_pair(g, bl, dl, r_s, ninv, 0, N - 1)  # pole to pole: out of reach
+    assert t0 == 0 and not np.any(M0)
+
+
+def test_block_pair_without_truncation_matches_harmonic_product():
+    """r_s = pi: the block between two rings is the sub-block of the harmonic
+    product Y diag(d) Y^T + (Y diag(b) Y^T)^T diag(N^-1) Y diag(b) Y^T."""
+    g = O.grid(8)
+    rng = np.random.default_rng(8)
+    bl = rng.uniform(0.2, 1.0, 9)
+    dl = rng.uniform(0.1, 1.0, 9)
+    ninv = rng.uniform(0.5, 2.0, g["npix"])
+    Bh = _harmonic_matrix(g, bl)
+    full = _harmonic_matrix(g, dl) + Bh.T @ np.diag(ninv) @ Bh
+    idx = [g["ring_offset"][j] + g["ring_stride"][j] * np.arange(g["nring"][j]) for j in range(g["nrings"])]
+    for j, k in [(0, 1), (2, 5), (4, 4), (8, 0)]:
+        M, _ = O.block_pair(g, bl, dl, math.pi, ninv, j, k)
+        ref = full[np.ix_(idx[j], idx[k])]
+        assert np.max(np.abs(M - ref)) <= 1e-12 * np.max(np.abs(full)), (j, k)
+
+
+def test_trisolve_matches_scipy():
+    from scipy.linalg import solve_triangular
+    rng = np.random.default_rng(33)
+    for n in (1, 2, 7, 60):
+        L = np.tril(rng.standard_normal((n, n))) + n * np.eye(n)
+        b = rng.standard_normal(n)
+        for trans in (False, True):
+            got = O.trisolve(L, b, trans)
+            ref = solve_triangular(L, b, lower=True, trans="T" if trans else "N")
+            np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14)
+    L = np.eye(3)
+    L[1, 1] = 0.0
+    with pytest.raises(ValueError):
+        O.trisolve(L, np.ones(3))
