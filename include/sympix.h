@@ -148,6 +148,13 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           128 (default 32) */
 #define SYMPIX_OPT_BORDER_THREADS 4   /* threads per CTA of the FP32 border pass: 256 or 512
                                           (default 512) */
+#define SYMPIX_OPT_NARROW_FACTOR 6    /* periodic-band blocks with w <= 12: 0 one warp per 4-8
+                                          blocks, G lanes per block sharing the band window; 1 the
+                                          earlier kernels (FP32: one lane per block on an FP32
+                                          band copy, a band warp and border warps per CTA; FP64 /
+                                          split FP32: lane groups); -1 (default) per arithmetic,
+                                          as measured at l_max 3000: FP64 0, FP32 1, split FP32 1.
+                                          sympix_autotune times both for its factor arithmetic */
 #define SYMPIX_OPT_WAIT_LIMIT 5       /* polls of a bounded device wait (default 2^22, about
                                           0.3 s): the FP32 factor's border warps wait for rows
                                           the band warp of the same CTA publishes */
@@ -156,6 +163,7 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
 int sympix_plan_option(sympix_plan_t plan, int option, double value);
 
 /* Autotune the launch shapes (SYMPIX_OPT_TABLE_CTA, SYMPIX_OPT_BORDER_THREADS)
+ * and the w <= 12 factor kernel of factor_precision (SYMPIX_OPT_NARROW_FACTOR)
  * on the caller's data: each candidate runs the calls it affects
  * (sympix_kernel_table with bl, dl; sympix_sample_blocks and
  * sympix_factor_blocks with ninv, storage, the precisions, blocks and info)
@@ -166,8 +174,9 @@ int sympix_plan_option(sympix_plan_t plan, int option, double value);
 int sympix_autotune(sympix_plan_t plan, const double *bl, const double *dl, const double *ninv, int storage,
                     int sample_precision, int factor_precision, double *blocks, int32_t *info, void *stream);
 
-/* The plan's launch shapes (either pointer may be NULL). */
-int sympix_plan_tuning(sympix_plan_t plan, int *table_cta, int *border_threads);
+/* The plan's launch shapes (any pointer may be NULL); narrow[3] receives
+ * the w <= 12 factor kernel per arithmetic (index SYMPIX_PREC_*). */
+int sympix_plan_tuning(sympix_plan_t plan, int *table_cta, int *border_threads, int *narrow);
 
 /* Per-kernel device times of the traced calls since the last read
  * (SYMPIX_OPT_TRACE): waits for the last recorded event, then writes up to
@@ -333,6 +342,47 @@ int sympix_factor_blocks(sympix_plan_t plan, int storage, int precision, double 
  *              calls on one plan must not overlap on the GPU.
  * Asynchronous. */
 int sympix_convolve(sympix_plan_t plan, const double *f, int precision, double *g, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Blocks between rings, and the preconditioner applied to a vector         */
+/* ------------------------------------------------------------------------ */
+
+/* Lay out the blocks M_jk between ring j and ring k = j + delta (delta >= 1)
+ * of every operator, for every ring j with both j and k in the planned range
+ * (Eq. system-rewritten and Eq. Dhat with rows on ring j and columns on ring
+ * k: M_qr = [gamma_qr <= r_s] d(x_qr) + sum_p B^_pq N^-1_p B^_pr, p over
+ * every pixel; M_kj = M_jk^T).  Entries vanish unless gamma_qr <= 2 r_s; row
+ * q of a block stores the columns r = r0(q) + t (mod n_k), t = 0 .. K-1,
+ * whose separation index z = (2q+1) Q - (2r+1) P (P = n_j / g, Q = n_k / g,
+ * g = gcd(n_j, n_k)) satisfies |z| <= zmax, with
+ * r0(q) = ceil(((2q+1) Q - zmax - P) / (2P)), zero past the row's own count;
+ * a block with K >= n_k stores every column (r0 = 0, K = n_k).  *bytes and
+ * *elements receive the size of the output buffer of sympix_sample_coupling.
+ * Host bookkeeping plus one upload; synchronous.  After the first call for
+ * any delta, sympix_kernel_table also evaluates d at the classes of
+ * different rings (D^ between rings); call it again before sampling. */
+int sympix_coupling_size(sympix_plan_t plan, int delta, size_t *bytes, int64_t *elements);
+
+/* Layout of the block (op, ring j) for ring offset delta: *offset (doubles)
+ * in the buffer and geom[7] = {rows n_j, columns n_k, K, zmax, P, Q,
+ * dense (1: every column stored)}. */
+int sympix_coupling_layout(sympix_plan_t plan, int delta, int op, int ring, int64_t *offset, int32_t *geom);
+
+/* Sample every block between ring j and ring j + delta (FP64) into out
+ * (device, sympix_coupling_size bytes) from ninv (device [nops][npix]) and the
+ * plan's kernel tables.  Asynchronous. */
+int sympix_sample_coupling(sympix_plan_t plan, const double *ninv, int delta, double *out, void *stream);
+
+/* The block preconditioner applied to x: y_j = M_jj^-1 x_j on every planned
+ * ring j of every operator (block Jacobi with the diagonal ring blocks), by
+ * forward and back substitution with the factors of sympix_factor_blocks.
+ *   blocks, info  the factored blocks of `storage` and their info array;
+ *   x, y          device FP64 [nops][npix] in pixel numbering (must not
+ *                 alias); y is written at the planned rings' pixels.  A block
+ *                 whose factorisation failed (info != 0) passes x through.
+ * FP64, one warp per block.  Asynchronous. */
+int sympix_apply(sympix_plan_t plan, int storage, const double *blocks, const int32_t *info, const double *x,
+                 double *y, void *stream);
 
 void sympix_plan_free(sympix_plan_t plan);
 

@@ -34,6 +34,7 @@
 // kernels), sympix_factor_f32.cu and sympix_factor_fused.cu (the FP32
 // path), sympix_factor_wide.cu (wide bands, dense blocks), this file (the
 // entry point).
+#include "sympix_chol.cuh"
 #include "sympix_factor_kernels.cuh"
 
 using namespace sympix;
@@ -48,16 +49,21 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
     cudaStream_t st = (cudaStream_t)stream;
     const bool dense = storage == SYMPIX_STORE_DENSE;
     trace_mark(pl, st, nullptr);
+    // periodic-band storage: bands up to w = 12 go to the narrow-band kernel
+    // (unless the plan selects the earlier kernels), 12 < w <= 16 to the
+    // lane kernels; dense storage keeps the lane kernels for every w <= 16
+    const bool narrow = !dense && pl->narrow_pref[precision] == 0;
+    if (narrow) launch_pband_chol(pl, precision, blocks, info, st);
     if (precision == SYMPIX_PREC_FP64) {
-        launch_band<ArF64>(pl, dense, blocks, info, st);
+        launch_band<ArF64>(pl, dense, blocks, info, st, 0, narrow);
         trace_mark(pl, st, "k_factor_band");
     } else if (precision == SYMPIX_PREC_FP32 && !dense) {
-        launch_f32_slices(pl, blocks, info, st);
+        launch_f32_slices(pl, blocks, info, st, narrow);
     } else if (precision == SYMPIX_PREC_FP32) {
         launch_band<ArF32>(pl, dense, blocks, info, st);
         trace_mark(pl, st, "k_factor_band");
     } else {
-        launch_band<ArF2>(pl, dense, blocks, info, st);
+        launch_band<ArF2>(pl, dense, blocks, info, st, 0, narrow);
         trace_mark(pl, st, "k_factor_band");
     }
     launch_factor_wide_dense(pl, precision, dense, blocks, info, st);

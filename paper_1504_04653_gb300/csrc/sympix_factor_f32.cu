@@ -121,15 +121,19 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
     }
 }
 
-void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only) {
     const int ns = (int)pl->f32_slices.size();
-    if (!ns) return;
+    const int nf = pl->f32_slices_fused;  // slices with w <= 12 (they come first)
+    if (hi_only ? ns == nf : ns == 0) return;
     const F32Slice *sl = pl->d_f32_slices.p;
-    k_f32_shadow_in<<<(unsigned)pl->f32_tiles.size(), 256, 0, st>>>(pl->d_f32_tiles.p, sl, pl->d_f32_items.p,
-                                                                   pl->d_blocks.p, blocks, pl->d_shadow_il.p);
+    const size_t nin = hi_only ? pl->f32_tiles_hi.size() : pl->f32_tiles.size();
+    const size_t nout = hi_only ? pl->f32_out_tiles_hi.size() : pl->f32_out_tiles.size();
+    const int2 *tin = hi_only ? pl->d_f32_tiles_hi.p : pl->d_f32_tiles.p;
+    const int2 *tout = hi_only ? pl->d_f32_out_tiles_hi.p : pl->d_f32_out_tiles.p;
+    k_f32_shadow_in<<<(unsigned)nin, 256, 0, st>>>(tin, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks,
+                                                   pl->d_shadow_il.p);
     trace_mark(pl, st, "k_f32_shadow_in");
-    const int nf = pl->f32_slices_fused;  // slices fused band + border (they come first)
-    if (nf > 0) launch_f32_fused(pl, nf, blocks, info, st);
+    if (nf > 0 && !hi_only) launch_f32_fused(pl, nf, blocks, info, st);
     if (ns > nf) {
         const size_t smem = (size_t)kF32BandStage * sizeof(float);
         cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -142,12 +146,11 @@ void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStre
             launch_f32_border<512>(pl, nf, ns - nf, blocks, info, st);
         trace_mark(pl, st, "k_f32_border_pass");
     }
-    k_f32_out<<<(unsigned)pl->f32_out_tiles.size(), 256, 0, st>>>(pl->d_f32_out_tiles.p, sl, pl->d_f32_items.p,
-                                                                 pl->d_blocks.p, info, pl->d_shadow_il.p,
-                                                                 pl->d_l21_il.p, blocks);
+    k_f32_out<<<(unsigned)nout, 256, 0, st>>>(tout, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
+                                             pl->d_l21_il.p, blocks);
     trace_mark(pl, st, "k_f32_out");
     // near-degenerate blocks: FP64 from the untouched FP64 input
-    launch_band<ArF64>(pl, false, blocks, info, st, 1);
+    launch_band<ArF64>(pl, false, blocks, info, st, 1, hi_only);
     trace_mark(pl, st, "k_factor_rescue");
 }
 

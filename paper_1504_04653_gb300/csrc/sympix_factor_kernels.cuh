@@ -638,9 +638,12 @@ __global__ void __launch_bounds__(NT) k_f32_border_pass(const F32Slice *__restri
 // the separate border pass of slices [first, first+count), NT threads per CTA
 template <int NT>
 void launch_f32_border(sympix_plan_t pl, int first, int count, double *blocks, int32_t *info, cudaStream_t st);
+// skip_narrow: lists 0 and 1 (w <= 12) are factored by the narrow-band kernel
 template <class A>
-void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue = 0);
-void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue = 0,
+                 bool skip_narrow = false);
+// hi_only: only the slices with w > 12 (the narrow-band kernel has the rest)
+void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only);
 void launch_f32_fused(sympix_plan_t pl, int nf, double *blocks, int32_t *info, cudaStream_t st);
 constexpr int kDefaultWaitLimit = 1 << 22;  // polls of a bounded device wait (about 0.3 s)
 void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,

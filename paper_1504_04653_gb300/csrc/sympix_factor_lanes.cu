@@ -479,10 +479,11 @@ __global__ void __launch_bounds__(128) k_factor_border_pass(int n0, int n1, int 
 // (twice the registers) run them for w <= 8 and factor wider bands with
 // lane groups.
 template <class A>
-void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue) {
+void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue,
+                 bool skip_narrow) {
     constexpr bool wide = std::is_same<A, ArF32>::value;
-    const int n0 = (int)pl->factor_items[0].size();
-    const int n1 = (int)pl->factor_items[1].size(), n2 = (int)pl->factor_items[2].size();
+    const int n0 = skip_narrow ? 0 : (int)pl->factor_items[0].size();
+    const int n1 = skip_narrow ? 0 : (int)pl->factor_items[1].size(), n2 = (int)pl->factor_items[2].size();
     const int w1 = wide ? n1 : 0, w2 = wide ? n2 : 0;
     const int32_t *i0 = pl->d_factor_items[0].p, *i1 = pl->d_factor_items[1].p, *i2 = pl->d_factor_items[2].p;
     if (n0 + w1 + w2 > 0) {
@@ -505,7 +506,7 @@ void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cu
     }
     if constexpr (!wide) {
         // wider bands: lane groups of 32 (band and border in one pass)
-        for (int l = 1; l <= 2; ++l) {
+        for (int l = skip_narrow ? 2 : 1; l <= 2; ++l) {
             const int nl = (int)pl->factor_items[l].size();
             if (!nl) continue;
             const unsigned grid = (unsigned)((nl * 32 + 127) / 128);
@@ -519,8 +520,8 @@ void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cu
     }
 }
 
-template void launch_band<ArF64>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int);
-template void launch_band<ArF32>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int);
-template void launch_band<ArF2>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int);
+template void launch_band<ArF64>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);
+template void launch_band<ArF32>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);
+template void launch_band<ArF2>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);
 
 }  // namespace sympix

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,11 @@ int cuda_error(cudaError_t e, const char *what);
 // Record a trace event on `st` (no-op unless the plan traces and `st` is not
 // capturing); `name` labels the span since the previous mark, null starts a call.
 void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
+
+// Widest band of the narrow-band factor (k_pband_chol), and the elements of
+// one tile of its FP32 commit.
+constexpr int kNarrowWMax = 12;
+constexpr int kCommitTileElems = 2048;
 
 // Smallest relative distance |u - u_s| / u_s a support class may have from
 // the coupling threshold before the radius is scaled by (1 - 1e-9).
@@ -56,11 +62,29 @@ struct WideClass {
 __global__ void k_split_ninv(int64_t count, const double *__restrict__ ninv, float *__restrict__ n32,
                              float *__restrict__ nlo);
 
-// Device buffer owned by a handle.
+// Device buffer owned by a handle.  Movable, not copyable: a copy would free
+// the memory twice.
 template <typename T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     int alloc(size_t count) {
         release();
         if (count == 0) return SYMPIX_OK;
@@ -154,12 +178,33 @@ struct F32Slice {
     int64_t sh, l21;
 };
 
+// One warp of the narrow-band factor: blocks chol_items[first .. first+count)
+// of exact width w <= 12, factored with g lanes each (count <= 32 / g).
+struct CholSlice {
+    int32_t w, first, count, g;
+};
+
 // One tile of the pixel-domain convolution: pixels q0 .. q0+127 of block
 // `block`'s ring, whose column c is output pixel goff + c * gstride.
 struct ConvItem {
     int32_t block, q0;
     int64_t goff;
     int32_t gstride, pad;
+};
+
+// One off-diagonal block (rows on ring j of block bj, columns on ring k of
+// block bk): pair constants P = n_j / g, Q = n_k / g, stored separations
+// |z| <= zmax in rows of K entries (every column when dense), at offset off;
+// dpair: the (j, k) entry of block bj (D^ between the rings), or -1.
+struct CoupDesc {
+    int64_t off;
+    int32_t bj, bk, n, K, zmax, P, Q, dense, dpair, pad;
+};
+
+struct CouplingPlan {
+    std::vector<CoupDesc> desc;
+    int64_t total = 0;  // stored entries
+    sympix::DevBuf<CoupDesc> d_desc;
 };
 
 struct sympix_plan_s {
@@ -195,6 +240,29 @@ struct sympix_plan_s {
     std::vector<int2> f32_tiles;  // (slice, first element) of the band shadow transposes
     std::vector<int2> f32_out_tiles;  // the same, then (slice, -1 - first element) of L21
     int f32_slices_fused = 0;     // slices with w <= 12, band and border fused (they come first)
+    // the f32 transposes of slices with w > 12 only (the narrow-band factor
+    // covers w <= 12 unless the two-role fused kernel is selected)
+    std::vector<int2> f32_tiles_hi, f32_out_tiles_hi;
+    int64_t size_shadow_hi = 0, size_l21_hi = 0;  // floats of the w > 12 slices (they come first in the buffers)
+    // narrow-band factor (w <= 12, periodic-band storage): blocks by width,
+    // most expensive first; slices for FP32 (8 lanes) and for FP64 / split
+    // FP32 (4 lanes up to w = 8, then 8); commit tiles (block, first element)
+    std::vector<int32_t> chol_items;
+    std::vector<CholSlice> chol_sl32, chol_sl64;
+    std::vector<int2> chol_tiles;
+    int chol_wmax = -1;
+    // per width: the slices [chol_f32[w], + chol_n32[w]) of chol_sl32 and
+    // [chol_f64[w], + chol_n64[w]) of chol_sl64; a stream per width present
+    // (the widths run side by side) and the fork / join events
+    int chol_f32[sympix::kNarrowWMax + 1] = {0}, chol_n32[sympix::kNarrowWMax + 1] = {0};
+    int chol_f64[sympix::kNarrowWMax + 1] = {0}, chol_n64[sympix::kNarrowWMax + 1] = {0};
+    cudaStream_t chol_st[sympix::kNarrowWMax + 1] = {nullptr};
+    cudaEvent_t chol_fork = nullptr, chol_join[sympix::kNarrowWMax + 1] = {nullptr};
+    // kernel for periodic bands w <= 12, per factor arithmetic (SYMPIX_PREC_*):
+    // 0 k_pband_chol (G lanes per block), 1 the earlier kernels (FP32: the
+    // two-role kernel on an FP32 band copy; FP64 / split FP32: lane groups).
+    // Defaults from measurement at l_max = 3000: FP64 0, FP32 1, split FP32 1.
+    int narrow_pref[3] = {0, 1, 1};
     int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;
@@ -218,8 +286,17 @@ struct sympix_plan_s {
     sympix::DevBuf<float> d_shadow_il;  // lane-interleaved FP32 band rows, w <= 16
     sympix::DevBuf<float> d_l21_il;     // lane-interleaved FP32 border rows, w <= 16
     sympix::DevBuf<int2> d_f32_out_tiles;
-    sympix::DevBuf<float> d_shadow;     // FP32 band rows of wide blocks, at their pband offsets
+    sympix::DevBuf<float> d_shadow;     // FP32 band rows of wide blocks / FP32 L11 of narrow ones, at their pband offsets
+    sympix::DevBuf<int32_t> d_chol_items;
+    sympix::DevBuf<CholSlice> d_chol_sl32, d_chol_sl64;
+    sympix::DevBuf<int2> d_chol_tiles, d_f32_tiles_hi, d_f32_out_tiles_hi;
     bool table_ready = false;
+    // blocks between rings: their layouts per ring offset; d evaluated at every
+    // class (not only the same-ring ones) once such a layout exists
+    std::map<int, CouplingPlan> coupling;
+    bool all_d = false, table_all_d = false;
+    sympix::DevBuf<int64_t> d_ring_off;  // the grid's ring offsets and strides (the apply's pixel addresses)
+    sympix::DevBuf<int32_t> d_ring_stride;
     // tracing (SYMPIX_OPT_TRACE): an event after every launch of a traced
     // call; a null name marks the start of a call
     int table_cta = 32, border_threads = 512;  // launch shapes (autotuned)
@@ -229,6 +306,11 @@ struct sympix_plan_s {
     int trace_n = 0;
     ~sympix_plan_s() {
         for (cudaEvent_t e : trace_ev) cudaEventDestroy(e);
+        for (int w = 0; w <= sympix::kNarrowWMax; ++w) {
+            if (chol_st[w]) cudaStreamDestroy(chol_st[w]);
+            if (chol_join[w]) cudaEventDestroy(chol_join[w]);
+        }
+        if (chol_fork) cudaEventDestroy(chol_fork);
     }
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
     // device status word (bit 1: a bounded wait ran out), read and cleared by

@@ -409,7 +409,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
 
     // FP32 factorisation on a band shadow: blocks by exact width (most
     // expensive first, so a slice holds blocks of similar length), slices of
-    // up to 32, each with its lane-interleaved shadow region
+    // up to 32, each with its lane-interleaved shadow region.  The slices of
+    // w > 12 take the first shadow offsets: the narrow-band factor covers
+    // w <= 12, so by default only those are allocated.
     {
         std::vector<int32_t> byw[17];
         for (int b : order) {
@@ -417,26 +419,49 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             if (bd.format == SYMPIX_BLOCK_PBAND && bd.w <= 16) byw[bd.w].push_back(b);
         }
         int64_t sh = 0, l21 = 0;
-        std::vector<int2> tiles21;
+        auto rows_of = [&](int w, int i, int cnt) {
+            int r = 0;
+            for (int j = 0; j < cnt; ++j) r = std::max(r, pl->blocks[byw[w][i + j]].n);
+            return r;
+        };
+        std::vector<int64_t> sh_at[17], l21_at[17];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int w = 0; w <= 16; ++w) {
+                if ((pass == 0) != (w > 12)) continue;
+                for (int i = 0; i < (int)byw[w].size(); i += 32) {
+                    const int rows = rows_of(w, i, std::min(32, (int)byw[w].size() - i));
+                    sh_at[w].push_back(sh);
+                    l21_at[w].push_back(l21);
+                    sh += 32 * (int64_t)rows * (w + 1);
+                    l21 += 32 * (int64_t)w * (rows - w);
+                }
+                if (pass == 0 && w == 16) {
+                    pl->size_shadow_hi = sh;
+                    pl->size_l21_hi = l21;
+                }
+            }
+        std::vector<int2> tiles21, tiles21_hi;
         for (int w = 0; w <= 16; ++w) {
             const int first = (int)pl->f32_items.size(), cnt = (int)byw[w].size();
             pl->f32_items.insert(pl->f32_items.end(), byw[w].begin(), byw[w].end());
-            for (int i = 0; i < cnt; i += 32) {
+            for (int i = 0, si = 0; i < cnt; i += 32, ++si) {
                 F32Slice sl;
                 sl.w = w;
                 sl.first = first + i;
                 sl.count = std::min(32, cnt - i);
-                sl.rows = 0;
-                for (int j = 0; j < sl.count; ++j) sl.rows = std::max(sl.rows, pl->blocks[byw[w][i + j]].n);
-                sl.sh = sh;
-                sl.l21 = l21;
+                sl.rows = rows_of(w, i, sl.count);
+                sl.sh = sh_at[w][si];
+                sl.l21 = l21_at[w][si];
                 const int64_t elems = (int64_t)sl.rows * (w + 1), elems21 = (int64_t)w * (sl.rows - w);
-                for (int64_t e0 = 0; e0 < elems; e0 += kTileE)
-                    pl->f32_tiles.push_back(make_int2((int)pl->f32_slices.size(), (int)e0));
-                for (int64_t e0 = 0; e0 < elems21; e0 += kTileE)
-                    tiles21.push_back(make_int2((int)pl->f32_slices.size(), (int)(-1 - e0)));
-                sh += 32 * elems;
-                l21 += 32 * elems21;
+                const int idx = (int)pl->f32_slices.size();
+                for (int64_t e0 = 0; e0 < elems; e0 += kTileE) {
+                    pl->f32_tiles.push_back(make_int2(idx, (int)e0));
+                    if (w > 12) pl->f32_tiles_hi.push_back(make_int2(idx, (int)e0));
+                }
+                for (int64_t e0 = 0; e0 < elems21; e0 += kTileE) {
+                    tiles21.push_back(make_int2(idx, (int)(-1 - e0)));
+                    if (w > 12) tiles21_hi.push_back(make_int2(idx, (int)(-1 - e0)));
+                }
                 if (w <= 12) ++pl->f32_slices_fused;
                 pl->f32_slices.push_back(sl);
             }
@@ -445,13 +470,55 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         pl->size_l21_il = l21;
         pl->f32_out_tiles = pl->f32_tiles;
         pl->f32_out_tiles.insert(pl->f32_out_tiles.end(), tiles21.begin(), tiles21.end());
+        pl->f32_out_tiles_hi = pl->f32_tiles_hi;
+        pl->f32_out_tiles_hi.insert(pl->f32_out_tiles_hi.end(), tiles21_hi.begin(), tiles21_hi.end());
+    }
+    if (cudaEventCreateWithFlags(&pl->chol_fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_error(SYMPIX_ECUDA, "sympix_support: event of the narrow-band factor"));
+    // narrow-band factor (w <= 12): blocks by width, most expensive first;
+    // FP32 slices of 4 blocks (8 lanes each), FP64 / split-FP32 slices of
+    // 8 blocks (4 lanes) up to w = 8 and 2 blocks (16 lanes) above; commit tiles over
+    // the band rows of every block
+    {
+        std::vector<int32_t> byw[kNarrowWMax + 1];
+        for (int b : order) {
+            const BlockDesc &bd = pl->blocks[b];
+            if (bd.format == SYMPIX_BLOCK_PBAND && bd.w <= kNarrowWMax) byw[bd.w].push_back(b);
+        }
+        for (int w = 0; w <= kNarrowWMax; ++w) {
+            const int first = (int)pl->chol_items.size(), cnt = (int)byw[w].size();
+            if (!cnt) continue;
+            pl->chol_wmax = w;
+            pl->chol_items.insert(pl->chol_items.end(), byw[w].begin(), byw[w].end());
+            const int g64 = w <= 8 ? 4 : 16;
+            pl->chol_f32[w] = (int)pl->chol_sl32.size();
+            pl->chol_f64[w] = (int)pl->chol_sl64.size();
+            for (int i = 0; i < cnt; i += 32 / 8) pl->chol_sl32.push_back({w, first + i, std::min(32 / 8, cnt - i), 8});
+            for (int i = 0; i < cnt; i += 32 / g64)
+                pl->chol_sl64.push_back({w, first + i, std::min(32 / g64, cnt - i), g64});
+            pl->chol_n32[w] = (int)pl->chol_sl32.size() - pl->chol_f32[w];
+            pl->chol_n64[w] = (int)pl->chol_sl64.size() - pl->chol_f64[w];
+            if (cudaStreamCreateWithFlags(&pl->chol_st[w], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&pl->chol_join[w], cudaEventDisableTiming) != cudaSuccess)
+                return fail(set_error(SYMPIX_ECUDA, "sympix_support: stream of the narrow-band factor"));
+            for (int b : byw[w]) {
+                const BlockDesc &bd = pl->blocks[b];
+                const int64_t lim = (int64_t)(bd.n - bd.w) * (bd.w + 1);
+                for (int64_t e0 = 0; e0 < lim; e0 += kCommitTileElems) pl->chol_tiles.push_back(make_int2(b, (int)e0));
+            }
+        }
     }
     if ((rc = pl->d_f32_items.upload(pl->f32_items)) || (rc = pl->d_f32_slices.upload(pl->f32_slices)) ||
-        (rc = pl->d_f32_tiles.upload(pl->f32_tiles)) ||
-        (rc = pl->d_f32_out_tiles.upload(pl->f32_out_tiles)) ||
+        (rc = pl->d_f32_tiles.upload(pl->f32_tiles)) || (rc = pl->d_f32_out_tiles.upload(pl->f32_out_tiles)) ||
+        (rc = pl->d_f32_tiles_hi.upload(pl->f32_tiles_hi)) ||
+        (rc = pl->d_f32_out_tiles_hi.upload(pl->f32_out_tiles_hi)) ||
         (rc = pl->d_shadow_il.alloc(std::max<int64_t>(pl->size_shadow_il, 1))) ||
         (rc = pl->d_l21_il.alloc(std::max<int64_t>(pl->size_l21_il, 1))) ||
-        (rc = pl->d_shadow.alloc(pl->factor_items[5].empty() ? 1 : std::max<int64_t>(pl->size_pband, 1))))
+        (rc = pl->d_chol_items.upload(pl->chol_items)) || (rc = pl->d_chol_sl32.upload(pl->chol_sl32)) ||
+        (rc = pl->d_chol_sl64.upload(pl->chol_sl64)) || (rc = pl->d_chol_tiles.upload(pl->chol_tiles)) ||
+        (rc = pl->d_shadow.alloc((pl->factor_items[5].empty() && pl->chol_items.empty())
+                                     ? 1
+                                     : std::max<int64_t>(pl->size_pband, 1))))
         return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
         (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_items_dense_rows.upload(pl->items_dense_rows)) || (rc = pl->d_items_conv.upload(pl->items_conv)))
@@ -460,7 +527,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         if ((rc = pl->d_items_pband[bkt].upload(pl->items_pband[bkt]))) return fail(rc);
     for (int l = 0; l < 6; ++l)
         if ((rc = pl->d_factor_items[l].upload(pl->factor_items[l]))) return fail(rc);
-    if ((rc = pl->d_status.alloc(1))) return fail(rc);
+    if ((rc = pl->d_status.alloc(1)) || (rc = pl->d_ring_off.upload(grid->offset)) ||
+        (rc = pl->d_ring_stride.upload(grid->stride)))
+        return fail(rc);
     if (cudaMemset(pl->d_status.p, 0, sizeof(int32_t)) != cudaSuccess)
         return fail(set_error(SYMPIX_ECUDA, "sympix_support: status word"));
     const size_t tabn = (size_t)nops * std::max<int64_t>(nslots, 1);
@@ -498,6 +567,18 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         pl->border_threads = (int)value;
         return SYMPIX_OK;
     }
+    if (option == SYMPIX_OPT_NARROW_FACTOR) {
+        if (value != 0.0 && value != 1.0 && value != -1.0)
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: narrow factor kernel is -1, 0 or 1");
+        if (value == -1.0) {
+            pl->narrow_pref[SYMPIX_PREC_FP64] = 0;
+            pl->narrow_pref[SYMPIX_PREC_FP32] = 1;
+            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
+        } else {
+            for (int &v : pl->narrow_pref) v = (int)value;
+        }
+        return SYMPIX_OK;
+    }
     if (option == SYMPIX_OPT_WAIT_LIMIT) {
         if (!(value >= 1.0) || value > 2147483647.0 || value != floor(value))
             return set_error(SYMPIX_EINVAL, "sympix_plan_option: wait limit is an integer in [1, 2^31)");
@@ -528,10 +609,12 @@ void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name) {
 }
 }  // namespace sympix
 
-extern "C" int sympix_plan_tuning(sympix_plan_t pl, int *table_cta, int *border_threads) {
+extern "C" int sympix_plan_tuning(sympix_plan_t pl, int *table_cta, int *border_threads, int *narrow) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_plan_tuning: NULL plan");
     if (table_cta) *table_cta = pl->table_cta;
     if (border_threads) *border_threads = pl->border_threads;
+    if (narrow)
+        for (int i = 0; i < 3; ++i) narrow[i] = pl->narrow_pref[i];
     return SYMPIX_OK;
 }
 
@@ -573,7 +656,28 @@ extern "C" int sympix_autotune(sympix_plan_t pl, const double *bl, const double 
         }
     }
     pl->table_cta = best_cta;
-    if (!rc && factor_precision == SYMPIX_PREC_FP32 && storage == SYMPIX_STORE_PBAND && !pl->f32_slices.empty()) {
+    // the w <= 12 factor kernel of this arithmetic (periodic-band storage)
+    if (!rc && storage == SYMPIX_STORE_PBAND && !pl->chol_items.empty() && factor_precision >= 0 &&
+        factor_precision <= 2) {
+        best = 1e30f;
+        int best_k = pl->narrow_pref[factor_precision];
+        for (int kk : {0, 1}) {
+            pl->narrow_pref[factor_precision] = kk;
+            float ms = 0.0f;
+            auto run = [&] {
+                int r = sympix_sample_blocks(pl, ninv, sample_precision, storage, blocks, st);
+                return r ? r : sympix_factor_blocks(pl, storage, factor_precision, blocks, info, st);
+            };
+            if ((rc = timed(run, &ms))) break;
+            if (ms < best) {
+                best = ms;
+                best_k = kk;
+            }
+        }
+        pl->narrow_pref[factor_precision] = best_k;
+    }
+    if (!rc && factor_precision == SYMPIX_PREC_FP32 && storage == SYMPIX_STORE_PBAND && !pl->f32_slices.empty() &&
+        pl->narrow_pref[SYMPIX_PREC_FP32] == 1) {
         best = 1e30f;
         int best_nt = pl->border_threads;
         for (int nt : {256, 512}) {
@@ -646,21 +750,37 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
     // mirrors the launch sequence of sympix_factor_blocks
     int f = 0;
     const bool pband = storage == SYMPIX_STORE_PBAND;
+    const bool narrow = pband && pl->narrow_pref[factor_precision] == 0;
     const bool l0 = !pl->factor_items[0].empty(), l1 = !pl->factor_items[1].empty(),
                l2 = !pl->factor_items[2].empty();
+    if (narrow && !pl->chol_items.empty()) {
+        // one launch per width present (FP32: then its commit and the FP64
+        // rescue, again one launch per width)
+        int n32 = 0, n64 = 0;
+        for (int w = 0; w <= kNarrowWMax; ++w) {
+            n32 += pl->chol_n32[w] > 0 ? 1 : 0;
+            n64 += pl->chol_n64[w] > 0 ? 1 : 0;
+        }
+        f += factor_precision == SYMPIX_PREC_FP32 ? n32 + 1 + n64 : n64;
+    }
     if (factor_precision == SYMPIX_PREC_FP32 && pband) {
-        if (!pl->f32_items.empty()) {
-            // shadow in, band pass, border pass (with the corners), FP64
-            // write-back, then the FP64 rescue launches (which return at
-            // once for blocks that need none)
-            const int nsl = (int)pl->f32_slices.size(), nfu = pl->f32_slices_fused;
-            f = 2 + (nfu > 0 ? 1 : 0) + (nsl > nfu ? 2 : 0);
+        const int nsl = (int)pl->f32_slices.size(), nfu = pl->f32_slices_fused;
+        if (narrow) {
+            // slices with w > 12: shadow in, band pass, border pass, write-back, FP64 rescue of list 2
+            if (nsl > nfu) f += 4 + (l2 ? 1 : 0);
+        } else if (nsl > 0) {
+            // shadow in, the fused kernel (w <= 12), band and border passes, FP64
+            // write-back, then the FP64 rescue launches (which return at once
+            // for blocks that need none)
+            f += 2 + (nfu > 0 ? 1 : 0) + (nsl > nfu ? 2 : 0);
             f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
-        f = (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
+        f += (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
+    } else if (narrow) {
+        f += l2 ? 1 : 0;  // lane groups for 12 < w <= 16
     } else {
-        f = (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
+        f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
     }
     f += (int)pl->wide_cls.size() * ((factor_precision == SYMPIX_PREC_FP32 && pband) ? 2 : 1);
     for (int l = 3; l < 5; ++l) f += pl->factor_items[l].empty() ? 0 : 1;
@@ -719,7 +839,11 @@ extern "C" int sympix_plan_device_bytes(sympix_plan_t pl, size_t *bytes, size_t 
                pl->d_blocks.bytes() + pl->d_entries.bytes() + pl->d_items_dense.bytes() +
                pl->d_items_dense_rows.bytes() + pl->d_items_conv.bytes() + pl->d_f32_items.bytes() +
                pl->d_f32_slices.bytes() + pl->d_f32_tiles.bytes() + pl->d_shadow_il.bytes() +
-               pl->d_l21_il.bytes() + pl->d_f32_out_tiles.bytes() + pl->d_shadow.bytes();
+               pl->d_l21_il.bytes() + pl->d_f32_out_tiles.bytes() + pl->d_shadow.bytes() + pl->d_chol_items.bytes() +
+               pl->d_chol_sl32.bytes() + pl->d_chol_sl64.bytes() + pl->d_chol_tiles.bytes() +
+               pl->d_f32_tiles_hi.bytes() + pl->d_f32_out_tiles_hi.bytes() + pl->d_status.bytes() +
+               pl->d_ring_off.bytes() + pl->d_ring_stride.bytes();
+    for (const auto &kv : pl->coupling) b += kv.second.d_desc.bytes();
     for (int i = 0; i < 5; ++i) b += pl->d_items_pband[i].bytes();
     for (int i = 0; i < 6; ++i) b += pl->d_factor_items[i].bytes();
     if (bytes) *bytes = b;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
                                                const double *__restrict__ cd, double *__restrict__ tb,
                                                double *__restrict__ td, float *__restrict__ tb32,
                                                float *__restrict__ tblo, float *__restrict__ td32,
-                                               float *__restrict__ tdlo) {
+                                               float *__restrict__ tdlo, int all_d) {
     constexpr int J = kTableSpt;
     const int L1 = lmax + 1;
     const int nops = min(NOPS, nops_total - op0);
@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
         s[j] = ((int64_t)blockIdx.x * J + j) * blockDim.x + threadIdx.x;
         ok[j] = s[j] < nslots;
         u[j] = ok[j] ? slot_u[s[j]] : 0.0;
-        same[j] = ok[j] && pairs[slot_pair[s[j]]].a == pairs[slot_pair[s[j]]].b;
+        // d at the same-ring classes (the diagonal blocks), or at every class
+        // once blocks between rings are planned
+        same[j] = ok[j] && (all_d || pairs[slot_pair[s[j]]].a == pairs[slot_pair[s[j]]].b);
         p[j] = 1.0;
         dlt[j] = -u[j];
 #pragma unroll
@@ -145,7 +147,7 @@ static int launch_table(sympix_plan_t pl, const double *bl, const double *dl, do
 #define SPX_TABLE(NO)                                                                                              \
     k_table<NO><<<grid, cta, 0, st>>>(pl->nslots, pl->nops, op0, lmax, pl->d_slot_u.p, pl->d_slot_pair.p,          \
                                       pl->d_pairs.p, rec, cb, cd, pl->d_tab_b.p, pl->d_tab_d.p, pl->d_tab_b32.p, \
-                                      pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p)
+                                      pl->d_tab_blo.p, pl->d_tab_d32.p, pl->d_tab_dlo.p, pl->all_d ? 1 : 0)
             if (chunk == 8)
                 SPX_TABLE(8);
             else if (chunk == 4)
@@ -162,6 +164,7 @@ static int launch_table(sympix_plan_t pl, const double *bl, const double *dl, do
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, who);
     pl->table_ready = true;
+    pl->table_all_d = pl->all_d;
     return SYMPIX_OK;
 }
 

@@ -18,6 +18,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libsympix.so"
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 OPT_FP32_PIVOT_FLOOR, OPT_TRACE, OPT_TABLE_CTA, OPT_BORDER_THREADS, OPT_WAIT_LIMIT = 1, 2, 3, 4, 5
+OPT_NARROW_FACTOR = 6
 LAYOUT_GREEDY, LAYOUT_DP = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32X2 = 0, 1, 2
 STORE_PBAND, STORE_DENSE = 0, 1
@@ -69,9 +70,13 @@ SIGNATURES = [
     ("sympix_sample_blocks", _i, [_vp, _vp, _i, _i, _vp, _vp]),
     ("sympix_factor_blocks", _i, [_vp, _i, _i, _vp, _vp, _vp]),
     ("sympix_autotune", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
-    ("sympix_plan_tuning", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    ("sympix_plan_tuning", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     ("sympix_trace_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), _i32p]),
     ("sympix_convolve", _i, [_vp, _vp, _i, _vp, _vp]),
+    ("sympix_coupling_size", _i, [_vp, _i, _sizep, _i64p]),
+    ("sympix_coupling_layout", _i, [_vp, _i, _i, _i, _i64p, _i32p]),
+    ("sympix_sample_coupling", _i, [_vp, _vp, _i, _vp, _vp]),
+    ("sympix_apply", _i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     ("sympix_plan_free", None, [_vp]),
     ("sympix_step_create", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_vp)]),
     ("sympix_step_launch", _i, [_vp, _i, _vp]),
@@ -208,8 +213,14 @@ class Plan:
     def tuning(self):
         """(table CTA size, border-pass threads) the plan launches with."""
         a, b = ctypes.c_int(), ctypes.c_int()
-        _check(lib().sympix_plan_tuning(self._h, ctypes.byref(a), ctypes.byref(b)))
+        _check(lib().sympix_plan_tuning(self._h, ctypes.byref(a), ctypes.byref(b), None))
         return a.value, b.value
+
+    def narrow_kernels(self):
+        """{arithmetic: 0 (G-lane kernel) or 1 (earlier kernels)} for w <= 12 bands."""
+        nk = (ctypes.c_int * 3)()
+        _check(lib().sympix_plan_tuning(self._h, None, None, nk))
+        return {"fp64": nk[0], "fp32": nk[1], "fp32x2": nk[2]}
 
     def autotune(self, bl, dl, ninv, blocks, info, storage="pband", sample_precision="fp32",
                  factor_precision="fp32", stream=None):
@@ -218,6 +229,10 @@ class Plan:
                                      PRECISIONS[sample_precision], PRECISIONS[factor_precision], _ptr(blocks),
                                      _ptr(info), _stream(stream)))
         return self.tuning()
+
+    def set_narrow_factor(self, kernel: int):
+        """w <= 12 bands: 0 the G-lane kernel, 1 the earlier kernels, -1 per arithmetic (default)."""
+        _check(lib().sympix_plan_option(self._h, OPT_NARROW_FACTOR, float(kernel)))
 
     def set_wait_limit(self, polls: int):
         """Polls of a bounded device wait (the FP32 factor's border warps)."""
@@ -259,6 +274,19 @@ class Plan:
         b, st = ctypes.c_size_t(), ctypes.c_size_t()
         _check(lib().sympix_plan_device_bytes(self._h, ctypes.byref(b), ctypes.byref(st)))
         return b.value, st.value
+
+    def coupling_size(self, delta=1):
+        """(bytes, elements) of the blocks between rings j and j + delta."""
+        b, e = ctypes.c_size_t(), ctypes.c_int64()
+        _check(lib().sympix_coupling_size(self._h, int(delta), ctypes.byref(b), ctypes.byref(e)))
+        return b.value, e.value
+
+    def coupling_layout(self, delta, op, ring):
+        """(offset, rows, cols, K, zmax, P, Q, dense) of the block (op, ring) -> (op, ring + delta)."""
+        off = ctypes.c_int64()
+        geom = (ctypes.c_int32 * 7)()
+        _check(lib().sympix_coupling_layout(self._h, int(delta), int(op), int(ring), ctypes.byref(off), geom))
+        return (off.value, *list(geom))
 
     def support(self, op, ring, radius):
         out = np.zeros(2 * radius + 1, np.int32)
@@ -389,6 +417,51 @@ def sympix_convolve(plan: Plan, f, precision="fp64", out=None, stream=None):
         raise SympixError(EINVAL, "g buffer too small")
     _check(lib().sympix_convolve(plan.handle, _ptr(f), PRECISIONS[precision], _ptr(out), _stream(stream)))
     return out
+
+
+def sympix_sample_coupling(plan: Plan, ninv, delta=1, out=None, stream=None):
+    """Blocks between rings j and j + delta (FP64); returns the buffer."""
+    import torch
+    if ninv.dtype != torch.float64 or tuple(ninv.shape) != (plan.nops, plan.grid.npix):
+        raise SympixError(EINVAL, f"ninv must be float64 [{plan.nops}, {plan.grid.npix}]")
+    nbytes, _ = plan.coupling_size(delta)
+    if out is None:
+        out = torch.empty(max(1, nbytes // 8), dtype=torch.float64, device=ninv.device)
+    elif out.numel() * 8 < nbytes:
+        raise SympixError(EINVAL, "coupling buffer too small")
+    _check(lib().sympix_sample_coupling(plan.handle, _ptr(ninv), int(delta), _ptr(out), _stream(stream)))
+    return out
+
+
+def sympix_apply(plan: Plan, blocks, info, x, storage="pband", out=None, stream=None):
+    """y = M^-1 x with the factored diagonal ring blocks (block Jacobi)."""
+    import torch
+    if x.dtype != torch.float64 or tuple(x.shape) != (plan.nops, plan.grid.npix):
+        raise SympixError(EINVAL, f"x must be float64 [{plan.nops}, {plan.grid.npix}]")
+    if out is None:
+        out = torch.zeros_like(x)
+    _check(lib().sympix_apply(plan.handle, STORAGES[storage], _ptr(blocks), _ptr(info), _ptr(x), _ptr(out),
+                              _stream(stream)))
+    return out
+
+
+def unpack_coupling(buf: np.ndarray, plan: Plan, delta: int, op: int, ring: int) -> np.ndarray:
+    """Dense n_j x n_k block between ring `ring` and ring + delta from a host
+    copy of the sympix_sample_coupling buffer."""
+    off, nj, nk, K, zmax, P, Q, dense = plan.coupling_layout(delta, op, ring)
+    rows = buf[off:off + nj * K].reshape(nj, K)
+    M = np.zeros((nj, nk))
+    for q in range(nj):
+        if dense:
+            M[q, :] = rows[q]
+            continue
+        Z = (2 * q + 1) * Q
+        r0 = -((-(Z - zmax - P)) // (2 * P))
+        for t in range(K):
+            r = r0 + t
+            if abs(Z - (2 * r + 1) * P) <= zmax:
+                M[q, r % nk] += rows[q, t]
+    return M
 
 
 # -- host-side views of the block buffer (for tests and users) -----------------------

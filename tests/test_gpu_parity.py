@@ -679,3 +679,109 @@ def test_chunked_tables(S, dev, nops):
             ref, _ = O.block(og, wl.beams()[o], wl.priors()[o], wl.radii()[o], r["ninv"][o], j)
             M = S.unpack_block(r["sampled"], r["plan"], "pband", o, j)
             assert _err(M, ref) <= TOL["fp64"], (o, j, _err(M, ref))
+
+
+# -- the narrow-band factor (w <= 12): every width, every arithmetic ------------
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("fprec", ["fp64", "fp32", "fp32x2"])
+def test_narrow_factor_every_width(S, dev, fprec, kernel):
+    """Operators whose radii give periodic-band widths from 0 to 12 at
+    l_max = 120: every such block's factor reproduces the sampled block
+    (L L^T), equals numpy's Cholesky of it, and its pivot verdict is numpy's;
+    blocks of every width, in both the 8-lane (FP32) and the 4 / 16-lane
+    (FP64, split FP32) slicings, including ragged slices."""
+    radii = np.array([0.004, 0.012, 0.021, 0.033, 0.047, 0.063, 0.081, 0.1, 0.125, 0.155])
+    nops = len(radii)
+    wl = W.Workload("narrow120", 120, [300.0] * nops, [0.0, 5, 10, 15, 20, 0, 5, 10, 15, 20][:nops],
+                    list(range(80, 80 + nops)))
+    import torch
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, radii)
+    plan.set_narrow_factor(kernel)
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(wl.ninv(colat), device=dev), precision="fp64")
+    r = {"sampled": blocks.cpu().numpy()}
+    r["info"] = S.sympix_factor_blocks(plan, blocks, precision=fprec).cpu().numpy()
+    r["factored"] = blocks.cpu().numpy()
+    nr = int(grid.nrings)
+    tol = {"fp64": 1e-12, "fp32x2": 1e-12, "fp32": 1e-6}[fprec]
+    seen = set()
+    for o in range(nops):
+        for j in range(nr):
+            _, n, w, fmt = plan.block_layout("pband", o, j)
+            if fmt != S.BLOCK_PBAND or w > 12:
+                continue
+            seen.add(int(w))
+            M = S.unpack_block(r["sampled"], plan, "pband", o, j)
+            try:
+                Lref = np.linalg.cholesky(M)
+                ok = True
+            except np.linalg.LinAlgError:
+                ok = False
+            info = int(r["info"][o * nr + j])
+            assert (info == 0) == ok, (o, j, n, w, info)
+            if ok:
+                L = S.unpack_block(r["factored"], plan, "pband", o, j, factored=True)
+                assert _err(L @ L.T, M) <= 10 * tol, (o, j, n, w, _err(L @ L.T, M))
+                assert _err(L, Lref) <= 1000 * tol, (o, j, n, w, _err(L, Lref))
+    assert len(seen) >= 6 and min(seen) <= 2 and max(seen) >= 10, sorted(seen)
+
+
+@pytest.mark.parametrize("fprec", ["fp64", "fp32", "fp32x2"])
+def test_narrow_factor_matches_earlier_kernels(S, dev, fprec):
+    """The G-lane narrow-band kernel and the earlier kernels (plan option 1)
+    factor the l_max = 500 blocks to the same result within the arithmetic's
+    rounding, with the same pivot verdicts."""
+    import torch
+    wl = W.WORKLOADS["lmax500"]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(wl.ninv(colat), device=dev), precision="fp64")
+    a, b = blocks.clone(), blocks.clone()
+    plan.set_narrow_factor(0)
+    ia = S.sympix_factor_blocks(plan, a, precision=fprec).cpu().numpy()
+    plan.set_narrow_factor(1)
+    ib = S.sympix_factor_blocks(plan, b, precision=fprec).cpu().numpy()
+    plan.set_narrow_factor(-1)
+    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 1, "fp32x2": 1}
+    assert np.array_equal(ia, ib) and np.all(ia == 0)
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    tol = {"fp64": 1e-13, "fp32x2": 1e-11, "fp32": 1e-5}[fprec]
+    for j in range(0, grid.nrings, 7):
+        La = S.unpack_block(A, plan, "pband", 0, j, factored=True)
+        Lb = S.unpack_block(B, plan, "pband", 0, j, factored=True)
+        assert _err(La, Lb) <= tol, (j, _err(La, Lb))
+
+
+def test_narrow_factor_fp32_rescue_restores_fp64(S, dev):
+    """With the pivot floor at 2 every FP32 narrow-band block is marked and
+    refactored in FP64 from its untouched input: FP64 accuracy, and the same
+    factor as the FP64 narrow kernel bit for bit."""
+    import torch
+    wl = W.WORKLOADS["lmax500"]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(wl.ninv(colat), device=dev), precision="fp64")
+    a, b = blocks.clone(), blocks.clone()
+    plan.set_narrow_factor(0)
+    plan.set_pivot_floor(2.0)
+    ia = S.sympix_factor_blocks(plan, a, precision="fp32").cpu().numpy()
+    plan.set_pivot_floor(0.05)
+    ib = S.sympix_factor_blocks(plan, b, precision="fp64").cpu().numpy()
+    assert np.all(ia == 0) and np.all(ib == 0)
+    # the FP64 rescue runs on the FP64 slicing, so the narrow blocks match bit for bit
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    for j in range(0, grid.nrings, 5):
+        _, n, w, fmt = plan.block_layout("pband", 0, j)
+        La = S.unpack_block(A, plan, "pband", 0, j, factored=True)
+        Lb = S.unpack_block(B, plan, "pband", 0, j, factored=True)
+        if fmt == S.BLOCK_PBAND and w <= 12:
+            assert np.array_equal(La, Lb), j
+        else:
+            assert _err(La, Lb) <= 1e-12, j

@@ -137,16 +137,22 @@ def test_trace_names_every_kernel():
     nothing recorded once tracing is off."""
     wl, grid, plan, colat, bl, dl, ninv = _setup("lmax500")
     plan.set_trace(True)
+    plan.set_narrow_factor(0)  # the G-lane kernel for every arithmetic
     S.sympix_kernel_table(plan, bl, dl)
     blocks = S.sympix_sample_blocks(plan, ninv, precision="fp32", storage="pband")
     S.sympix_factor_blocks(plan, blocks, storage="pband", precision="fp32")
     spans = plan.trace_read()
     names = [n for n, _ in spans]
-    for k in ("k_table", "k_split_ninv", "k_sample_pband", "k_f32_shadow_in", "k_f32_out"):
+    for k in ("k_table", "k_split_ninv", "k_sample_pband", "k_pband_chol", "k_chol_commit", "k_pband_chol_rescue"):
         assert k in names, names
-    # band and border passes: fused for widths up to 12, separate above
-    assert "k_f32_fused" in names or {"k_f32_band_pass", "k_f32_border_pass"} <= set(names), names
     assert all(ms >= 0.0 for _, ms in spans)
+    # the earlier FP32 kernels: shadow transposes and the fused band / border kernel
+    plan.set_narrow_factor(1)
+    S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp32"), precision="fp32")
+    names = [n for n, _ in plan.trace_read()]
+    for k in ("k_f32_shadow_in", "k_f32_fused", "k_f32_out", "k_factor_rescue"):
+        assert k in names, names
+    plan.set_narrow_factor(-1)
     assert plan.trace_read() == []
     plan.set_trace(False)
     S.sympix_kernel_table(plan, bl, dl)
