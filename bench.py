@@ -54,6 +54,9 @@ def parse(argv=None):
     ap.add_argument("--launch", default="graph", choices=["graph", "eager"],
                     help="replay the step as captured CUDA graphs, or call the entry points directly")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--narrow-factor", type=int, default=None, choices=[-1, 0, 1],
+                    help="kernel for bands w <= 12: 0 G-lane, 1 earlier kernels, -1 per arithmetic "
+                         "(default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the l_max 1500 and 32-operator sub-lines")
@@ -330,11 +333,16 @@ def roofline(name, ms, model, hbm, pk):
 # kernel's sources hash to the digest recorded with the capture.
 KERNEL_SOURCES = {
     "k_table": ["sympix_table.cu"],
-    "k_pband_chol": ["sympix_chol.cuh", "sympix_chol_f32.cu", "sympix_arith.cuh", "sympix_internal.cuh"],
+    "k_f32_fused": ["sympix_factor_fused.cu", "sympix_factor_kernels.cuh", "sympix_arith.cuh"],
+    "k_pband_chol": ["sympix_chol.cuh", "sympix_chol_f32.cu", "sympix_chol_f64.cu", "sympix_chol_f2.cu",
+                     "sympix_arith.cuh"],
     "k_sample_pband": ["sympix_sample_kernels.cuh", "sympix_sample_f32.cu", "sympix_sample.cu"],
 }
 TRAFFIC = {
-    # (workload, precision, kernel): (bytes per launch, source digest, date and capture)
+    # (workload, precision, kernel): (bytes per launch, source digest, capture)
+    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_fused"): (
+        1692465408, "d2fbd52d0923",
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass over the bench's own mixed step"),
 }
 
 
@@ -525,9 +533,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     P = Problem(S, W, wl, dev, stream, flush, args.launch)
     plan, grid, elements = P.plan, P.grid, P.elements
-    if not args.no_autotune:
+    if not args.no_autotune and args.narrow_factor is None:
         P.autotune(args.precision)
         torch.cuda.synchronize()
+    if args.narrow_factor is not None:
+        plan.set_narrow_factor(args.narrow_factor)
 
     clocks = Clocks(local)
     main_st = P.timed(args.precision, args.steps, args.warmup, world)

@@ -19,11 +19,13 @@ __global__ void __launch_bounds__(256) k_chol_commit(const int2 *__restrict__ ti
 }
 
 
-// the widths present run on their own streams: fork from `st`, join back
+// the widths present run on their own streams (and the lane groups on a side
+// stream): fork from `st`, join back
 static void chol_fork(sympix_plan_t pl, cudaStream_t st) {
     cudaEventRecord(pl->chol_fork, st);
     for (int w = 0; w <= kNarrowWMax; ++w)
         if (pl->chol_st[w]) cudaStreamWaitEvent(pl->chol_st[w], pl->chol_fork, 0);
+    if (pl->chol_side) cudaStreamWaitEvent(pl->chol_side, pl->chol_fork, 0);
 }
 static void chol_join(sympix_plan_t pl, cudaStream_t st) {
     for (int w = 0; w <= kNarrowWMax; ++w)
@@ -31,26 +33,33 @@ static void chol_join(sympix_plan_t pl, cudaStream_t st) {
             cudaEventRecord(pl->chol_join[w], pl->chol_st[w]);
             cudaStreamWaitEvent(st, pl->chol_join[w], 0);
         }
+    if (pl->chol_side) {
+        cudaEventRecord(pl->chol_side_join, pl->chol_side);
+        cudaStreamWaitEvent(st, pl->chol_side_join, 0);
+    }
 }
 
 void launch_pband_chol(sympix_plan_t pl, int precision, double *blocks, int32_t *info, cudaStream_t st) {
-    if (pl->chol_items.empty()) return;
+    if (pl->chol_items.empty() && pl->factor_items[2].empty()) return;
     chol_fork(pl, st);
-    if (precision == SYMPIX_PREC_FP32)
-        launch_chol_f32(pl, blocks, info, 0);
-    else if (precision == SYMPIX_PREC_FP64)
-        launch_chol_f64(pl, blocks, info, 0);
-    else
-        launch_chol_f2(pl, blocks, info, 0);
+    if (precision == SYMPIX_PREC_FP32) {
+        launch_chol_f32(pl, blocks, info, 0, kCholWMax);
+    } else if (precision == SYMPIX_PREC_FP64) {
+        launch_chol_f64(pl, blocks, info, 0, kCholGroupFrom - 1);
+        if (pl->chol_side) launch_band_groups<ArF64>(pl, blocks, info, pl->chol_side);
+    } else {
+        launch_chol_f2(pl, blocks, info, 0, kCholGroupFrom - 1);
+        if (pl->chol_side) launch_band_groups<ArF2>(pl, blocks, info, pl->chol_side);
+    }
     chol_join(pl, st);
     trace_mark(pl, st, "k_pband_chol");
-    if (precision == SYMPIX_PREC_FP32) {
+    if (precision == SYMPIX_PREC_FP32 && !pl->chol_items.empty()) {
         k_chol_commit<<<(unsigned)pl->chol_tiles.size(), 256, 0, st>>>(pl->d_chol_tiles.p, pl->d_blocks.p, info,
                                                                       pl->d_shadow.p, blocks);
         trace_mark(pl, st, "k_chol_commit");
         // blocks whose FP32 pivots fell below the floor: FP64 from their input
         chol_fork(pl, st);
-        launch_chol_f64(pl, blocks, info, 1);
+        launch_chol_f64(pl, blocks, info, 1, kCholWMax);
         chol_join(pl, st);
         trace_mark(pl, st, "k_pband_chol_rescue");
     }

@@ -348,12 +348,20 @@ __global__ void __launch_bounds__(256) k_chol_commit(const int2 *__restrict__ ti
 // (slices [first, first + count) of the FP32 or the FP64 list), each on its
 // own stream so that the widths run side by side; one translation unit per
 // arithmetic.
-void launch_chol_f32(sympix_plan_t pl, double *blocks, int32_t *info, int rescue);
-void launch_chol_f64(sympix_plan_t pl, double *blocks, int32_t *info, int rescue);
-void launch_chol_f2(sympix_plan_t pl, double *blocks, int32_t *info, int rescue);
+void launch_chol_f32(sympix_plan_t pl, double *blocks, int32_t *info, int rescue, int wmax);
+void launch_chol_f64(sympix_plan_t pl, double *blocks, int32_t *info, int rescue, int wmax);
+void launch_chol_f2(sympix_plan_t pl, double *blocks, int32_t *info, int rescue, int wmax);
 
-// Launch the narrow-band factor of `precision` over the plan's w <= 12
-// periodic-band blocks (FP32: the pass, the commit, then the FP64 rescue).
+// FP64 and split FP32: widths up to kCholGroupFrom - 1 on k_pband_chol, wider
+// bands (up to 16) on the 32-lane group kernel, side by side (measured at
+// l_max 3000: the G-lane kernel is faster for w <= 8, the lane groups for
+// w = 9 .. 11, whose few long chains the G-lane kernel runs on one warp each)
+constexpr int kCholGroupFrom = 9;
+
+// Launch the narrow-band factor of `precision`: FP32 over the plan's w <= 12
+// periodic-band blocks (the pass, the commit, then the FP64 rescue); FP64 and
+// split FP32 over w <= 16 (the G-lane kernel below kCholGroupFrom, the lane
+// groups above, on a side stream).
 void launch_pband_chol(sympix_plan_t pl, int precision, double *blocks, int32_t *info, cudaStream_t st);
 
 }  // namespace sympix

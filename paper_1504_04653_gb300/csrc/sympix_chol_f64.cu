@@ -4,11 +4,11 @@
 
 namespace sympix {
 
-void launch_chol_f64(sympix_plan_t pl, double *blocks, int32_t *info, int rescue) {
+void launch_chol_f64(sympix_plan_t pl, double *blocks, int32_t *info, int rescue, int wmax) {
     auto one = [&](auto WWc) {
         constexpr int WW = decltype(WWc)::value;
         const int cnt = pl->chol_n64[WW];
-        if (!cnt) return;
+        if (!cnt || WW > wmax) return;
         constexpr int G = chol_lanes<ArF64>(WW);
         constexpr size_t smem = chol_smem_bytes<ArF64, WW, G>();
         auto kern = k_pband_chol<ArF64, WW, G>;

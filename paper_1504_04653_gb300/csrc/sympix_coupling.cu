@@ -20,9 +20,9 @@
 // The preconditioner M^-1 x applied block by block (the diagonal ring
 // blocks, block Jacobi): y = L^-T L^-1 x with the factor of
 // sympix_factor_blocks, one warp per block.  Periodic band: the band rows by
-// substitution along the band (the w products of a row summed by the warp),
-// the border rows as dense dot products; the back substitution adds the
-// border rows' column entries to every band row.
+// substitution along the band (one lane, from rows staged in shared memory),
+// the border rows as dense dot products; the back substitution first takes
+// the border rows' entries out of every band row, in parallel.
 #include <cmath>
 
 #include "sympix_internal.cuh"
@@ -119,12 +119,22 @@ __global__ void __launch_bounds__(128) k_sample_coupling(int64_t total, const Co
 
 // y = M^-1 x on every planned block (one warp per block): forward
 // substitution L z = x, back substitution L^T y = z, in FP64.  Blocks whose
-// factorisation failed (info != 0) pass x through unchanged.
+// factorisation failed (info != 0) pass x through unchanged.  The band
+// recurrences are sequential: 32 band rows at a time are staged into shared
+// memory by the warp (with their reciprocal diagonals), then one lane runs
+// the rows from there; the border rows (dense dot products) and their
+// contribution to every band row of the back substitution are formed by the
+// whole warp.
+constexpr int kApplyRows = 32;
+
 __global__ void __launch_bounds__(32) k_apply(const BlockDesc *__restrict__ blocks, const int32_t *__restrict__ info,
                                               const double *__restrict__ Lbuf, int dense_storage,
                                               const int64_t *__restrict__ roff, const int32_t *__restrict__ rstr,
-                                              int64_t npix, const double *__restrict__ x, double *__restrict__ y) {
-    extern __shared__ double v[];  // the block's vector, n values
+                                              int64_t npix, int max_ring, const double *__restrict__ x,
+                                              double *__restrict__ y) {
+    extern __shared__ double smem_apply[];
+    double *v = smem_apply;           // the block's vector, n values
+    double *stg = v + max_ring;       // staged band rows
     const int bi = blockIdx.x, lane = threadIdx.x;
     const BlockDesc bd = blocks[bi];
     const int n = bd.n;
@@ -148,14 +158,28 @@ __global__ void __launch_bounds__(32) k_apply(const BlockDesc *__restrict__ bloc
         const int w = bd.w, RL = w + 1, m = n - w;
         const double *band = Lbuf + bd.off_pband;
         const double *bord = band + (int64_t)n * RL;
-        // forward: band rows i < m, then the border rows
-        for (int i = 0; i < m; ++i) {
-            double s = 0.0;
-            for (int d = 1 + lane; d <= w && d <= i; d += 32) s = fma(band[(int64_t)i * RL + d], v[i - d], s);
-            s = wsum(s);
-            if (lane == 0) v[i] = (v[i] - s) / band[(int64_t)i * RL];
+        double *rinv = stg + (kApplyRows + w) * RL;  // 1 / L[i][i] of the staged rows
+        // stage band rows [r0, r1) and their reciprocal diagonals
+        auto stage = [&](int r0, int r1) {
+            const int cnt = (r1 - r0) * RL;
+            for (int e = lane; e < cnt; e += 32) stg[e] = band[(int64_t)r0 * RL + e];
+            for (int r = lane; r < r1 - r0; r += 32) rinv[r] = 1.0 / band[(int64_t)(r0 + r) * RL];
+            __syncwarp();
+        };
+        // forward: band rows i < m
+        for (int r0 = 0; r0 < m; r0 += kApplyRows) {
+            const int r1 = min(m, r0 + kApplyRows);
+            stage(r0, r1);
+            if (lane == 0)
+                for (int i = r0; i < r1; ++i) {
+                    const double *row = stg + (i - r0) * RL;
+                    double s = v[i];
+                    for (int d = 1; d <= w && d <= i; ++d) s = fma(-row[d], v[i - d], s);
+                    v[i] = s * rinv[i - r0];
+                }
             __syncwarp();
         }
+        // forward: the border rows (dense dot products)
         for (int b = 0; b < w; ++b) {
             const int i = m + b;
             double s = 0.0;
@@ -164,20 +188,32 @@ __global__ void __launch_bounds__(32) k_apply(const BlockDesc *__restrict__ bloc
             if (lane == 0) v[i] = (v[i] - s) / bord[(int64_t)b * n + i];
             __syncwarp();
         }
-        // back: the border rows (columns i >= m of L^T), then the band rows
-        for (int i = n - 1; i >= m; --i) {
-            double s = 0.0;
-            for (int c = i + 1 + lane; c < n; c += 32) s = fma(bord[(int64_t)(c - m) * n + i], v[c], s);
-            s = wsum(s);
-            if (lane == 0) v[i] = (v[i] - s) / bord[(int64_t)(i - m) * n + i];
-            __syncwarp();
+        // back: the border rows (columns i >= m of L^T)
+        if (lane == 0)
+            for (int i = n - 1; i >= m; --i) {
+                double s = v[i];
+                for (int c = i + 1; c < n; ++c) s = fma(-bord[(int64_t)(c - m) * n + i], v[c], s);
+                v[i] = s / bord[(int64_t)(i - m) * n + i];
+            }
+        __syncwarp();
+        // their contribution to every band row: v_i -= sum_b L21[b][i] v_{m+b}
+        for (int i = lane; i < m; i += 32) {
+            double s = v[i];
+            for (int b = 0; b < w; ++b) s = fma(-bord[(int64_t)b * n + i], v[m + b], s);
+            v[i] = s;
         }
-        for (int i = m - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int d = 1 + lane; d <= w && i + d < m; d += 32) s = fma(band[(int64_t)(i + d) * RL + d], v[i + d], s);
-            for (int b = lane; b < w; b += 32) s = fma(bord[(int64_t)b * n + i], v[m + b], s);
-            s = wsum(s);
-            if (lane == 0) v[i] = (v[i] - s) / band[(int64_t)i * RL];
+        __syncwarp();
+        // back: band rows, from the bottom; a chunk needs the w rows below it
+        for (int r1 = m; r1 > 0; r1 -= kApplyRows) {
+            const int r0 = max(0, r1 - kApplyRows);
+            const int re = min(m, r1 + w);
+            stage(r0, re);
+            if (lane == 0)
+                for (int i = r1 - 1; i >= r0; --i) {
+                    double s = v[i];
+                    for (int d = 1; d <= w && i + d < m; ++d) s = fma(-stg[(i + d - r0) * RL + d], v[i + d], s);
+                    v[i] = s * rinv[i - r0];
+                }
             __syncwarp();
         }
     } else {
@@ -326,12 +362,16 @@ extern "C" int sympix_apply(sympix_plan_t pl, int storage, const double *blocks,
         return set_error(SYMPIX_EINVAL, "sympix_apply: unknown storage %d", storage);
     if (x == y) return set_error(SYMPIX_EINVAL, "sympix_apply: x and y must not alias");
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t smem = (size_t)pl->grid->max_ring * sizeof(double);
+    // the vector, then kApplyRows + w staged rows of w + 1 values and their
+    // reciprocal diagonals (the widest periodic band planned)
+    const size_t W1 = (size_t)pl->max_w + 1;
+    const size_t smem = ((size_t)pl->grid->max_ring + (kApplyRows + W1) * (W1 + 1)) * sizeof(double);
     cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     trace_mark(pl, st, nullptr);
     k_apply<<<(unsigned)pl->blocks.size(), 32, smem, st>>>(pl->d_blocks.p, info, blocks,
                                                            storage == SYMPIX_STORE_DENSE ? 1 : 0, pl->d_ring_off.p,
-                                                           pl->d_ring_stride.p, pl->grid->npix, x, y);
+                                                           pl->d_ring_stride.p, pl->grid->npix, pl->grid->max_ring,
+                                                           x, y);
     trace_mark(pl, st, "k_apply");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "sympix_apply: launch");

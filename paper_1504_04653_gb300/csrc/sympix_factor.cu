@@ -55,7 +55,7 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
     const bool narrow = !dense && pl->narrow_pref[precision] == 0;
     if (narrow) launch_pband_chol(pl, precision, blocks, info, st);
     if (precision == SYMPIX_PREC_FP64) {
-        launch_band<ArF64>(pl, dense, blocks, info, st, 0, narrow);
+        if (!narrow) launch_band<ArF64>(pl, dense, blocks, info, st);  // (narrow: every w <= 16 done)
         trace_mark(pl, st, "k_factor_band");
     } else if (precision == SYMPIX_PREC_FP32 && !dense) {
         launch_f32_slices(pl, blocks, info, st, narrow);
@@ -63,7 +63,7 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
         launch_band<ArF32>(pl, dense, blocks, info, st);
         trace_mark(pl, st, "k_factor_band");
     } else {
-        launch_band<ArF2>(pl, dense, blocks, info, st, 0, narrow);
+        if (!narrow) launch_band<ArF2>(pl, dense, blocks, info, st);
         trace_mark(pl, st, "k_factor_band");
     }
     launch_factor_wide_dense(pl, precision, dense, blocks, info, st);

@@ -642,6 +642,9 @@ void launch_f32_border(sympix_plan_t pl, int first, int count, double *blocks, i
 template <class A>
 void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cudaStream_t st, int rescue = 0,
                  bool skip_narrow = false);
+// the 32-lane group kernel on lists 1 and 2 (8 < w <= 16, periodic band) on `st`
+template <class A>
+void launch_band_groups(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
 // hi_only: only the slices with w > 12 (the narrow-band kernel has the rest)
 void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only);
 void launch_f32_fused(sympix_plan_t pl, int nf, double *blocks, int32_t *info, cudaStream_t st);

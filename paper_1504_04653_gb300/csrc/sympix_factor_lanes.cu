@@ -520,6 +520,18 @@ void launch_band(sympix_plan_t pl, bool dense, double *blocks, int32_t *info, cu
     }
 }
 
+template <class A>
+void launch_band_groups(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    for (int l = 1; l <= 2; ++l) {
+        const int nl = (int)pl->factor_items[l].size();
+        if (!nl) continue;
+        k_factor_band<A, 32, false><<<(unsigned)((nl * 32 + 127) / 128), 128, 0, st>>>(
+            nl, pl->d_factor_items[l].p, pl->d_blocks.p, blocks, info, 0);
+    }
+}
+template void launch_band_groups<ArF64>(sympix_plan_t, double *, int32_t *, cudaStream_t);
+template void launch_band_groups<ArF2>(sympix_plan_t, double *, int32_t *, cudaStream_t);
+
 template void launch_band<ArF64>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);
 template void launch_band<ArF32>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);
 template void launch_band<ArF2>(sympix_plan_t, bool, double *, int32_t *, cudaStream_t, int, bool);

@@ -258,6 +258,8 @@ struct sympix_plan_s {
     int chol_f64[sympix::kNarrowWMax + 1] = {0}, chol_n64[sympix::kNarrowWMax + 1] = {0};
     cudaStream_t chol_st[sympix::kNarrowWMax + 1] = {nullptr};
     cudaEvent_t chol_fork = nullptr, chol_join[sympix::kNarrowWMax + 1] = {nullptr};
+    cudaStream_t chol_side = nullptr;  // the lane-group kernel beside the narrow kernels (FP64, split FP32)
+    cudaEvent_t chol_side_join = nullptr;
     // kernel for periodic bands w <= 12, per factor arithmetic (SYMPIX_PREC_*):
     // 0 k_pband_chol (G lanes per block), 1 the earlier kernels (FP32: the
     // two-role kernel on an FP32 band copy; FP64 / split FP32: lane groups).
@@ -311,6 +313,8 @@ struct sympix_plan_s {
             if (chol_join[w]) cudaEventDestroy(chol_join[w]);
         }
         if (chol_fork) cudaEventDestroy(chol_fork);
+        if (chol_side) cudaStreamDestroy(chol_side);
+        if (chol_side_join) cudaEventDestroy(chol_side_join);
     }
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
     // device status word (bit 1: a bounded wait ran out), read and cleared by

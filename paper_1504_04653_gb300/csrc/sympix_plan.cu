@@ -475,6 +475,10 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     }
     if (cudaEventCreateWithFlags(&pl->chol_fork, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_error(SYMPIX_ECUDA, "sympix_support: event of the narrow-band factor"));
+    if ((!pl->factor_items[1].empty() || !pl->factor_items[2].empty()) &&
+        (cudaStreamCreateWithFlags(&pl->chol_side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&pl->chol_side_join, cudaEventDisableTiming) != cudaSuccess))
+        return fail(set_error(SYMPIX_ECUDA, "sympix_support: stream of the lane-group factor"));
     // narrow-band factor (w <= 12): blocks by width, most expensive first;
     // FP32 slices of 4 blocks (8 lanes each), FP64 / split-FP32 slices of
     // 8 blocks (4 lanes) up to w = 8 and 2 blocks (16 lanes) above; commit tiles over
@@ -761,7 +765,9 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
             n32 += pl->chol_n32[w] > 0 ? 1 : 0;
             n64 += pl->chol_n64[w] > 0 ? 1 : 0;
         }
-        f += factor_precision == SYMPIX_PREC_FP32 ? n32 + 1 + n64 : n64;
+        int n64lo = 0;  // FP64 / split FP32: the G-lane kernel below kCholGroupFrom (9)
+        for (int w = 0; w < 9; ++w) n64lo += pl->chol_n64[w] > 0 ? 1 : 0;
+        f += factor_precision == SYMPIX_PREC_FP32 ? n32 + 1 + n64 : n64lo;
     }
     if (factor_precision == SYMPIX_PREC_FP32 && pband) {
         const int nsl = (int)pl->f32_slices.size(), nfu = pl->f32_slices_fused;
@@ -778,7 +784,7 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
     } else if (factor_precision == SYMPIX_PREC_FP32) {
         f += (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
     } else if (narrow) {
-        f += l2 ? 1 : 0;  // lane groups for 12 < w <= 16
+        f += (l1 ? 1 : 0) + (l2 ? 1 : 0);  // lane groups for 8 < w <= 16, beside the G-lane kernel
     } else {
         f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
     }

@@ -775,13 +775,14 @@ def test_narrow_factor_fp32_rescue_restores_fp64(S, dev):
     plan.set_pivot_floor(0.05)
     ib = S.sympix_factor_blocks(plan, b, precision="fp64").cpu().numpy()
     assert np.all(ia == 0) and np.all(ib == 0)
-    # the FP64 rescue runs on the FP64 slicing, so the narrow blocks match bit for bit
+    # the FP64 rescue runs the FP64 G-lane kernel on the FP64 slicing, as the FP64
+    # factor does for w <= 8 (wider bands go to the lane groups there): bit for bit
     A, B = a.cpu().numpy(), b.cpu().numpy()
     for j in range(0, grid.nrings, 5):
         _, n, w, fmt = plan.block_layout("pband", 0, j)
         La = S.unpack_block(A, plan, "pband", 0, j, factored=True)
         Lb = S.unpack_block(B, plan, "pband", 0, j, factored=True)
-        if fmt == S.BLOCK_PBAND and w <= 12:
+        if fmt == S.BLOCK_PBAND and w <= 8:
             assert np.array_equal(La, Lb), j
         else:
             assert _err(La, Lb) <= 1e-12, j
