@@ -54,9 +54,9 @@ def parse(argv=None):
     ap.add_argument("--launch", default="graph", choices=["graph", "eager"],
                     help="replay the step as captured CUDA graphs, or call the entry points directly")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    ap.add_argument("--narrow-factor", type=int, default=None, choices=[-1, 0, 1],
-                    help="kernel for bands w <= 12: 0 G-lane, 1 earlier kernels, -1 per arithmetic "
-                         "(default: the autotuner's choice)")
+    ap.add_argument("--narrow-factor", type=int, default=None, choices=[-1, 0, 1, 2, 3],
+                    help="kernel for bands w <= 12: 0 G-lane, 1 earlier kernels, 2 FP32 chunked border, "
+                         "3 FP32 split CTAs, -1 per arithmetic (default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the l_max 1500 and 32-operator sub-lines")
@@ -296,6 +296,17 @@ def kernel_models(plan, grid, sprec, fprec):
     fl = sum(factor_work(n, w, True)[0] for n, w in narrow)
     fl12 = sum(factor_work(n, w, True)[0] for n, w in narrow if w <= 12)
     b12 = 16.0 * sum(n * (w + 1) for n, w in narrow if w <= 12)
+    fl8 = sum(factor_work(n, w, True)[0] for n, w in narrow if w <= 8)
+    b8 = 16.0 * sum(n * (w + 1) for n, w in narrow if w <= 8)
+    # the split launch (option 3) factors the w <= 8 blocks; its span ends on
+    # the main stream, and the w 9..12 path beside it shows only as the
+    # remainder after it ("k_f32_split"), which is not a kernel's own time
+    m.update({"k_f32_split_w8": (b8, fl8, "fp32"), "k_f32_fused_w8": (b8, fl8, "fp32"),
+              "k_f32_split": (0.0, None, "fp32", "the w 9..12 path's time beyond the w <= 8 launch, not a kernel")})
+    # option 2 (band pass of every slice, border rows by column chunks): its
+    # chunk kernels are not modelled separately
+    for name in ("k_l21_transfer", "k_l21_carry", "k_l21_solve", "k_l21_cornerpart", "k_l21_corner"):
+        m[name] = (0.0, None, "fp32", "a phase of the chunked border solve, not modelled alone")
     m.update({"k_f32_shadow_in": (band * 12.0, 0.0, "fp32"), "k_f32_out": (band * 4.0 + l21 * 12.0, 0.0, "fp32"),
               "k_f32_fused": (b12, fl12, "fp32"), "k_f32_band_pass": (16.0 * band - b12, (fl - fl12) / 3, "fp32"),
               "k_f32_border_pass": (0.0, 2 * (fl - fl12) / 3, "fp32"),
@@ -308,13 +319,14 @@ def roofline(name, ms, model, hbm, pk):
     or flops / the peak of their arithmetic."""
     if name not in model:
         return {"kernel": name, "ms": ms, "bound": "unmodelled", "frac": None}
-    byt, fl, typ = model[name]
+    byt, fl, typ = model[name][:3]
+    note = model[name][3] if len(model[name]) > 3 else "work depends on the data"
     t_hbm = byt / hbm
     t_alu = (fl / pk[typ][0]) if fl else 0.0
     r = {"kernel": name, "ms": ms, "bytes": byt, "flops": fl, "flop_type": typ,
          "t_hbm_ms": t_hbm * 1e3, "t_alu_ms": t_alu * 1e3}
     if fl is None and byt == 0.0:
-        r.update({"bound": "unmodelled", "frac": None, "note": "work depends on the data"})
+        r.update({"bound": "unmodelled", "frac": None, "note": note})
     elif t_hbm >= t_alu:
         r.update({"bound": "hbm", "achieved": byt / (ms * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                   "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"})
@@ -334,15 +346,20 @@ def roofline(name, ms, model, hbm, pk):
 KERNEL_SOURCES = {
     "k_table": ["sympix_table.cu"],
     "k_f32_fused": ["sympix_factor_fused.cu", "sympix_factor_kernels.cuh", "sympix_arith.cuh"],
+    "k_f32_split_w8": ["sympix_factor_split.cu", "sympix_factor_kernels.cuh", "sympix_arith.cuh"],
     "k_pband_chol": ["sympix_chol.cuh", "sympix_chol_f32.cu", "sympix_chol_f64.cu", "sympix_chol_f2.cu",
                      "sympix_arith.cuh"],
     "k_sample_pband": ["sympix_sample_kernels.cuh", "sympix_sample_f32.cu", "sympix_sample.cu"],
 }
 TRAFFIC = {
     # (workload, precision, kernel): (bytes per launch, source digest, capture)
-    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_fused"): (
-        1692465408, "d2fbd52d0923",
+    ("lmax3000_fwhm5", "fp32:fp32", "k_table"): (
+        799488, "e053756e1e7a",
         "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass over the bench's own mixed step"),
+    ("lmax3000_fwhm5", "fp32:fp32", "k_f32_split_w8"): (
+        1544984320, "76d769407ff2",
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_f32_split<8,256,2>, one pass over the bench's "
+        "own mixed step"),
 }
 
 

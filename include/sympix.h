@@ -152,9 +152,15 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           blocks, G lanes per block sharing the band window; 1 the
                                           earlier kernels (FP32: one lane per block on an FP32
                                           band copy, a band warp and border warps per CTA; FP64 /
-                                          split FP32: lane groups); -1 (default) per arithmetic,
-                                          as measured at l_max 3000: FP64 0, FP32 1, split FP32 1.
-                                          sympix_autotune times both for its factor arithmetic */
+                                          split FP32: lane groups); 2 FP32: the band pass alone,
+                                          then the border rows solved in parallel over column
+                                          chunks; 3 FP32: for w <= 8 band and border passes in two
+                                          CTAs of one cooperative launch (the kernel of 1 where
+                                          they cannot all be resident), 9 <= w <= 12 as 2 beside
+                                          it (2, 3: FP64 / split FP32 as 1); -1 (default) per
+                                          arithmetic, as measured at l_max 3000: FP64 0, FP32 3,
+                                          split FP32 1.  sympix_autotune times the candidates for
+                                          its factor arithmetic */
 #define SYMPIX_OPT_WAIT_LIMIT 5       /* polls of a bounded device wait (default 2^22, about
                                           0.3 s): the FP32 factor's border warps wait for rows
                                           the band warp of the same CTA publishes */
@@ -207,7 +213,8 @@ int sympix_plan_launches(sympix_plan_t plan, int storage, int sample_precision, 
 int sympix_blocks_size(sympix_plan_t plan, int storage, size_t *bytes, int64_t *elements);
 
 /* Where block (op, ring) sits in the blocks buffer of a storage mode:
- * offset in doubles, ring size n, lower band half-width w, format
+ * offset in doubles (a multiple of 4: every block starts on a 32-byte
+ * boundary), ring size n, lower band half-width w, format
  * SYMPIX_BLOCK_PBAND or SYMPIX_BLOCK_DENSE.
  *   PBAND format: n (2w+1) doubles.  Sampled: band[q*(w+1) + d] =
  *   M[q][(q-d) mod n] for d = 0..w (the other entries follow by symmetry).
@@ -309,6 +316,9 @@ int sympix_sample_blocks(sympix_plan_t plan, const double *ninv, int precision, 
                          double *blocks, void *stream);
 
 /* Cholesky-factor every sampled block in place, M = L L^T.
+ *   blocks     the sampled blocks (sympix_sample_blocks), 16-byte aligned
+ *              (cudaMalloc and PyTorch allocations are); SYMPIX_EINVAL
+ *              otherwise.
  *   precision  arithmetic of the periodic-band factorisation:
  *              SYMPIX_PREC_FP64, SYMPIX_PREC_FP32X2 (split FP32, near-FP64
  *              accuracy on the FP32 pipes) or SYMPIX_PREC_FP32.  With FP32

@@ -42,6 +42,8 @@ using namespace sympix;
 extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision, double *blocks, int32_t *info,
                                     void *stream) {
     if (!pl || !blocks || !info) return set_error(SYMPIX_EINVAL, "sympix_factor_blocks: NULL argument");
+    if ((reinterpret_cast<uintptr_t>(blocks) & 15) != 0)
+        return set_error(SYMPIX_EINVAL, "sympix_factor_blocks: blocks must be 16-byte aligned");
     if (storage != SYMPIX_STORE_PBAND && storage != SYMPIX_STORE_DENSE)
         return set_error(SYMPIX_EINVAL, "sympix_factor_blocks: unknown storage %d", storage);
     if (precision < SYMPIX_PREC_FP64 || precision > SYMPIX_PREC_FP32X2)

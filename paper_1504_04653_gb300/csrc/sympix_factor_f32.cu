@@ -29,20 +29,33 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
         s_cnt[threadIdx.x] = cnt;
     }
     __syncthreads();
+    // FP64 side: two consecutive elements of one block per thread (blocks
+    // start on 32-byte boundaries and e0 is even, so the pair is aligned)
 #pragma unroll
-    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
-        const int L = i / kTileE, e = i % kTileE;
-        float v = 0.0f;
-        if (e0 + e < s_cnt[L]) v = f64_to_f32_bits(out[s_off[L] + e0 + e]);
-        tile[e][L] = v;
+    for (int i = threadIdx.x; i < 16 * kTileE; i += 256) {
+        const int L = i / (kTileE / 2), e = 2 * (i % (kTileE / 2));
+        float v0 = 0.0f, v1 = 0.0f;
+        const int cnt = s_cnt[L];
+        if (e0 + e + 1 < cnt) {
+            const double2 d = *reinterpret_cast<const double2 *>(out + s_off[L] + e0 + e);
+            v0 = f64_to_f32_bits(d.x);
+            v1 = f64_to_f32_bits(d.y);
+        } else if (e0 + e < cnt) {
+            v0 = f64_to_f32_bits(out[s_off[L] + e0 + e]);
+        }
+        tile[e][L] = v0;
+        tile[e + 1][L] = v1;
     }
     __syncthreads();
+    // shadow side: four consecutive blocks of one element per thread
     const int lim = sl.rows * RL;
     float *dst = sh + sl.sh + (int64_t)e0 * 32;
 #pragma unroll
-    for (int i = threadIdx.x; i < 32 * kTileE; i += 256) {
-        const int e = i >> 5, L = i & 31;
-        if (e0 + e < lim) dst[e * 32 + L] = tile[e][L];
+    for (int i = threadIdx.x; i < 8 * kTileE; i += 256) {
+        const int e = i >> 3, L = 4 * (i & 7);
+        if (e0 + e < lim)
+            *reinterpret_cast<float4 *>(dst + e * 32 + L) =
+                make_float4(tile[e][L], tile[e][L + 1], tile[e][L + 2], tile[e][L + 3]);
     }
 }
 
@@ -98,25 +111,43 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
     const int kc = sl.rows - W;
     const int lim = part21 ? W * kc : sl.rows * RL;
     const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
+    // shadow side: four consecutive blocks of one element per thread
 #pragma unroll
-    for (int i = threadIdx.x; i < kTileE * 32; i += 256) {
-        const int e = i >> 5, L = i & 31;
-        tile[e][L] = (e0 + e < lim) ? src[e * 32 + L] : 0.0f;
+    for (int i = threadIdx.x; i < 8 * kTileE; i += 256) {
+        const int e = i >> 3, L = 4 * (i & 7);
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e0 + e < lim) v = *reinterpret_cast<const float4 *>(src + e * 32 + L);
+        tile[e][L] = v.x;
+        tile[e][L + 1] = v.y;
+        tile[e][L + 2] = v.z;
+        tile[e][L + 3] = v.w;
     }
     __syncthreads();
-    // every element of this thread has the same e (its lanes differ): the
-    // element's (row, offset) or (border row, column) is formed once
-    const int e = threadIdx.x % kTileE, ee = e0 + e;
+    // FP64 side: two consecutive elements of one block per thread; their
+    // (row, offset) or (border row, column) are formed once for all blocks.
+    // A pair that is contiguous and 16-byte aligned in the block (always in
+    // the band part: blocks start on 32-byte boundaries, e0 is even) goes as
+    // one 16-byte store.
+    const int e = 2 * (threadIdx.x % (kTileE / 2)), ee = e0 + e;
     if (ee >= lim) return;
-    const int q = part21 ? ee / kc : ee / RL;          // border row b, or band row
-    const int r = part21 ? ee - q * kc : ee - q * RL;  // column k, or offset d
+    const bool has2 = ee + 1 < lim;
+    const int q0 = part21 ? ee / kc : ee / RL;           // border row b, or band row
+    const int r0 = part21 ? ee - q0 * kc : ee - q0 * RL;  // column k, or offset d
+    const int q1 = part21 ? (ee + 1) / kc : (ee + 1) / RL;
+    const int r1 = part21 ? ee + 1 - q1 * kc : ee + 1 - q1 * RL;
 #pragma unroll
-    for (int L = threadIdx.x / kTileE; L < 32; L += 256 / kTileE) {
+    for (int L = threadIdx.x / (kTileE / 2); L < 32; L += 256 / (kTileE / 2)) {
         const int n = s_n[L], m = n - W;
-        const bool ok = s_live[L] && (part21 ? r < m : (q < m && r <= q));
-        if (ok) {
-            const int64_t dst = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q * n + r : s_off[L] + ee;
-            out[dst] = f32_to_f64_bits(tile[e][L]);
+        const bool ok0 = s_live[L] && (part21 ? r0 < m : (q0 < m && r0 <= q0));
+        const bool ok1 = has2 && s_live[L] && (part21 ? r1 < m : (q1 < m && r1 <= q1));
+        const int64_t d0 = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q0 * n + r0 : s_off[L] + ee;
+        const int64_t d1 = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q1 * n + r1 : s_off[L] + ee + 1;
+        if (ok0 && ok1 && d1 == d0 + 1 && (d0 & 1) == 0) {
+            *reinterpret_cast<double2 *>(out + d0) =
+                make_double2(f32_to_f64_bits(tile[e][L]), f32_to_f64_bits(tile[e + 1][L]));
+        } else {
+            if (ok0) out[d0] = f32_to_f64_bits(tile[e][L]);
+            if (ok1) out[d1] = f32_to_f64_bits(tile[e + 1][L]);
         }
     }
 }
@@ -133,7 +164,45 @@ void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStre
     k_f32_shadow_in<<<(unsigned)nin, 256, 0, st>>>(tin, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks,
                                                    pl->d_shadow_il.p);
     trace_mark(pl, st, "k_f32_shadow_in");
-    if (nf > 0 && !hi_only) launch_f32_fused(pl, nf, blocks, info, st);
+    if (nf > 0 && !hi_only) {
+        if (pl->narrow_pref[SYMPIX_PREC_FP32] == 2) {  // band pass, then the border rows by column chunks
+            const size_t smem = (size_t)kF32BandStage * sizeof(float);
+            cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_f32_band_pass<<<(unsigned)nf, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, pl->d_shadow_il.p,
+                                                           info, (float)pl->fp32_pivot_floor);
+            trace_mark(pl, st, "k_f32_band_pass");
+            launch_f32_l21(pl, blocks, info, st);
+        } else if (pl->narrow_pref[SYMPIX_PREC_FP32] == 3 && f32_split_fits(pl)) {
+            // w <= 8: band and border passes in separate CTAs of one launch;
+            // 9 <= w <= 12 (a few slices): band pass, then the chunked border
+            // kernels, on the side stream at the same time (a second
+            // cooperative launch would wait for the first to finish)
+            const int n8 = pl->f32_slices_w8;
+            const bool side = n8 > 0 && nf > n8 && pl->f32_side;
+            cudaStream_t sh = side ? pl->f32_side : st;
+            if (side) {
+                cudaEventRecord(pl->f32_fork, st);
+                cudaStreamWaitEvent(sh, pl->f32_fork, 0);
+            }
+            if (nf > n8) {
+                const size_t smem = (size_t)kF32BandStage * sizeof(float);
+                cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_f32_band_pass<<<(unsigned)(nf - n8), 32, smem, sh>>>(sl + n8, pl->d_f32_items.p, pl->d_blocks.p,
+                                                                      pl->d_shadow_il.p, info,
+                                                                      (float)pl->fp32_pivot_floor);
+                launch_f32_l21(pl, blocks, info, sh, true);
+            }
+            launch_f32_split_w8(pl, blocks, info, st);
+            if (side) trace_mark(pl, st, "k_f32_split_w8");
+            if (side) {
+                cudaEventRecord(pl->f32_join, sh);
+                cudaStreamWaitEvent(st, pl->f32_join, 0);
+            }
+            trace_mark(pl, st, "k_f32_split");
+        } else {
+            launch_f32_fused(pl, nf, blocks, info, st);
+        }
+    }
     if (ns > nf) {
         const size_t smem = (size_t)kF32BandStage * sizeof(float);
         cudaFuncSetAttribute(k_f32_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -245,9 +245,9 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
             StaticFor<0, RL>::run(part);
         }
         if (bad) m = 0;  // stop this lane; the warp keeps staging
-        // every 4th period: this period's L rows reach L2 (where the border
+        // every 8th period: this period's L rows reach L2 (where the border
         // pass stages from) before the flag says rows < (p+1)(W+1) are final
-        const bool publish = prog && (p & 3) == 3;
+        const bool publish = prog && (p & 7) == 7;
         if (publish) __threadfence();
         __syncwarp();    // every lane is done with the buffer the next copies overwrite
         if (publish && lane == 0) *prog = p + 1;
@@ -303,15 +303,26 @@ constexpr int kF32BandStage = 2 * 17 * 17 * 32;  // floats: two periods of W = 1
 // the device status bit kStatusTimeout, the sweep stops at the next
 // barrier (every thread reads the flag after the same barrier), waits for
 // its copies in flight, and reports kInfoTimeout for the slice's blocks.
+// SPLIT: the band pass runs in another CTA of the same (cooperative)
+// launch; the progress and a done flag are global words of the slice, the
+// function's NT threads are the whole CTA, and the band-pass results are read
+// from global memory once the done flag is seen (that wait is bounded too).
 constexpr int32_t kStatusTimeout = 1;  // bit of the plan's device status word
 constexpr int32_t kInfoTimeout = -1;   // info of a block whose factor a timed-out wait left incomplete
 struct FusedWait {
-    volatile int *prog;    // periods of L11 rows the band warp has published (shared)
-    const int *bandres;    // band-pass result per block (shared)
+    volatile int *prog;    // periods of L11 rows the band warp has published
+    const int *bandres;    // band-pass result per block
     volatile int *abort;   // set when a wait ran out (shared, starts 0)
     int32_t *status;       // device status word of the plan
     int limit;             // polls per wait
+    volatile int *done;    // split mode: set once bandres is final
 };
+
+// How the border role meets its band pass: after it (a separate kernel),
+// beside it in the same CTA (warp 0, shared-memory progress and a named
+// barrier at the end), or beside it in another CTA of the same launch
+// (global progress and done flags, each poll bounded).
+constexpr int kBorderAfter = 0, kBorderFused = 1, kBorderSplit = 2;
 
 // Barrier of all 32 + NT threads of the fused kernel (the band warp and the
 // border threads arrive from different code paths, which the non-aligned
@@ -321,13 +332,14 @@ __device__ __forceinline__ void fused_barrier_all() {
     asm volatile("barrier.sync 2, %0;\n" ::"n"(32 + NT) : "memory");
 }
 
-template <int W, int NT, bool FUSED>
+template <int W, int NT, int MODE>
 __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__restrict__ shs, float *__restrict__ l21,
                                            const double *__restrict__ out, const int64_t *s_off, const int *s_n,
                                            const int *s_live, float *stage, int *binfo, const FusedWait *fw) {
     constexpr int RL = W + 1, CH = RL * RL;
     constexpr int NWARP = NT / 32;
     constexpr int R = (W + NWARP - 1) / NWARP;  // border rows per lane
+    constexpr bool FUSED = MODE == kBorderFused, WAITS = MODE != kBorderAfter;
     const int tb = (int)threadIdx.x - (FUSED ? 32 : 0);
     auto bsync = [] {
         if (FUSED)
@@ -342,18 +354,27 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     const PBandView view{const_cast<double *>(out) + s_off[lane],
                          const_cast<double *>(out) + s_off[lane] + (int64_t)n * RL, n, W, m};
     const int kc = sl.rows - W;
+    int seen = 0;  // the largest progress value this thread has read
     auto issue = [&](int per) {
         const int r0 = per * RL;
         if (r0 < kc) {  // rows r0 .. r0 + W < the slice's rows
             bool ready = true;
-            if (FUSED) {  // wait until the band warp has finished these rows
-                int spins = 0;
-                while (*fw->prog < per + 1 && ++spins < fw->limit) __nanosleep(64);
-                __threadfence_block();
-                if (*fw->prog < per + 1) {  // ran out: stop the sweep at the next barrier
+            if (WAITS && seen < per + 1) {  // wait until the band warp has finished these rows
+                int spins = 0, v = *fw->prog;
+                while (v < per + 1 && ++spins < fw->limit) {
+                    __nanosleep(64);
+                    v = *fw->prog;
+                }
+                if (v < per + 1) {  // ran out: stop the sweep at the next barrier
                     ready = false;
                     *fw->abort = 1;
                     atomicOr(fw->status, kStatusTimeout);
+                } else {  // a newly published value: order the row reads after it (once per value)
+                    seen = v;
+                    if (FUSED)
+                        __threadfence_block();
+                    else
+                        __threadfence();  // the rows come from another SM's writes
                 }
             }
             if (ready) {
@@ -388,57 +409,30 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
 #pragma unroll
         for (int c = 0; c < RL; ++c) y[r][c] = 0.0f;
     }
-    // column k = p RL + PH; src = this lane's staged rows of period p
-    // TAIL: some block of the warp reaches its last W columns (A21's band
-    // part) or its end in this period; otherwise no select is needed
-    auto column = [&](auto PHc, auto FIRSTc, auto TAILc, const float *src, int kbase) {
-        constexpr int PH = decltype(PHc)::value;
-        constexpr bool FIRST = decltype(FIRSTc)::value;  // p == 0: mask the columns left of 0
-        constexpr bool TAIL = decltype(TAILc)::value;
-        const int k = kbase + PH;
-        const float *row = src + PH * RL * 32;  // L11 row k: offset d at row[32 d]
-        float lr[RL];
-#pragma unroll
-        for (int d = 0; d < RL; ++d) lr[d] = row[d * 32];
-        const float rd = rsqrtf(lr[0]);
-        const float rcp = rd * rd;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int b = b0 + r;
-            float acc = 0.0f;
-            if constexpr (FIRST && PH < W) acc = aw[r][PH < W ? PH : 0];
-            if constexpr (TAIL) {  // the last W columns, without a branch
-                const int c = k - (m - W);
-                const float a = abuf[((b < W ? b : W - 1) * W + min(max(c, 0), W - 1)) * 32 + lane];
-                acc = (c >= 0 && c < W) ? a : acc;
-            }
-#pragma unroll
-            for (int cc = 0; cc < W; ++cc) {
-                if (FIRST && PH - W + cc < 0) continue;  // left of column 0
-                acc = fmaf(-y[r][(PH - W + cc + RL) % RL], lr[W - cc], acc);
-            }
-            const float val = (!TAIL || (live && b < W && k < m)) ? acc * rcp : 0.0f;
-            y[r][PH] = val;
-            if (b < W) {
-                vb[(b * RL + PH) * 32 + lane] = val;
-                if (!TAIL || k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
-            }
-        }
-    };
     // corner sums S[b][b2] = sum_k L21[b][k] L21[b2][k], b2 <= b, lane =
     // block; each period's L21 values pass through vbuf.  With one border
     // row per warp (R = 1) a pair goes to the warp owning one of its rows
     // (b when b + b2 is odd or b = b2, else b2), which takes that operand
     // from its own registers: one shared load per FMA, about (W+1)/2 + 1
     // pairs per warp.  Otherwise the pairs are dealt round-robin.
+    // With a single border warp (R = W) every pair's operands are the lane's
+    // own registers: the sums are formed per column, no shared memory.
     constexpr int NPAIR = W * (W + 1) / 2, NP = (NPAIR + NWARP - 1) / NWARP;
-    constexpr bool OWN = R == 1;
-    constexpr int NPC = OWN ? (W + 1) / 2 + 1 : (NP > 0 ? NP : 1);
+    constexpr bool REG = NWARP == 1;
+    constexpr bool OWN = R == 1 && !REG;
+    constexpr int NPC = REG ? (NPAIR > 0 ? NPAIR : 1) : OWN ? (W + 1) / 2 + 1 : (NP > 0 ? NP : 1);
     const int wq = tb >> 5;
     int pb[NPC], pb2[NPC], po[NPC];
     float sacc[NPC];
     int npw = 0;  // pairs of this warp
-    if constexpr (OWN) {
+    if constexpr (REG) {
+#pragma unroll
+        for (int i = 0; i < NPC; ++i) {
+            pb[i] = pb2[i] = po[i] = 0;
+            sacc[i] = 0.0f;
+        }
+        npw = NPAIR;
+    } else if constexpr (OWN) {
 #pragma unroll
         for (int i = 0; i < NPC; ++i) {
             pb[i] = pb2[i] = po[i] = 0;
@@ -472,19 +466,67 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
             if (wq + NWARP * i < NPAIR) npw = i + 1;
         }
     }
-    auto accumulate = [&](const float *v) {
+    // column k = p RL + PH; src = this lane's staged rows of period p
+    // TAIL: some block of the warp reaches its last W columns (A21's band
+    // part) or its end in this period; otherwise no select is needed
+    auto column = [&](auto PHc, auto FIRSTc, auto TAILc, const float *src, int kbase) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr bool FIRST = decltype(FIRSTc)::value;  // p == 0: mask the columns left of 0
+        constexpr bool TAIL = decltype(TAILc)::value;
+        const int k = kbase + PH;
+        const float *row = src + PH * RL * 32;  // L11 row k: offset d at row[32 d]
+        float lr[RL];
 #pragma unroll
-        for (int i = 0; i < NPC; ++i) {
-            if (i >= npw) break;
-            if constexpr (OWN) {
-                const float *z = v + po[i] * RL * 32 + lane;
+        for (int d = 0; d < RL; ++d) lr[d] = row[d * 32];
+        const float rd = rsqrtf(lr[0]);
+        const float rcp = rd * rd;
 #pragma unroll
-                for (int c = 0; c < RL; ++c) sacc[i] = fmaf(y[0][c], z[c * 32], sacc[i]);
-            } else {
-                const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
-#pragma unroll
-                for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+        for (int r = 0; r < R; ++r) {
+            const int b = b0 + r;
+            float acc = 0.0f;
+            if constexpr (FIRST && PH < W) acc = aw[r][PH < W ? PH : 0];
+            if constexpr (TAIL) {  // the last W columns, without a branch
+                const int c = k - (m - W);
+                const float a = abuf[((b < W ? b : W - 1) * W + min(max(c, 0), W - 1)) * 32 + lane];
+                acc = (c >= 0 && c < W) ? a : acc;
             }
+#pragma unroll
+            for (int cc = 0; cc < W; ++cc) {
+                if (FIRST && PH - W + cc < 0) continue;  // left of column 0
+                acc = fmaf(-y[r][(PH - W + cc + RL) % RL], lr[W - cc], acc);
+            }
+            const float val = (!TAIL || (live && b < W && k < m)) ? acc * rcp : 0.0f;
+            y[r][PH] = val;
+            if (b < W) {
+                if constexpr (!REG) vb[(b * RL + PH) * 32 + lane] = val;
+                if (!TAIL || k < kc) l21[((int64_t)b * kc + k) * 32 + lane] = val;
+            }
+        }
+        if constexpr (REG) {  // S[b][b2] += L21[b][k] L21[b2][k], pair index b (b+1)/2 + b2
+#pragma unroll
+            for (int b = 0; b < W; ++b)
+#pragma unroll
+                for (int b2 = 0; b2 <= b; ++b2)
+                    sacc[b * (b + 1) / 2 + b2] = fmaf(y[b][PH], y[b2][PH], sacc[b * (b + 1) / 2 + b2]);
+        }
+    };
+    auto accumulate = [&](const float *v) {
+        if constexpr (!REG) {
+#pragma unroll
+            for (int i = 0; i < NPC; ++i) {
+                if (i >= npw) break;
+                if constexpr (OWN) {
+                    const float *z = v + po[i] * RL * 32 + lane;
+#pragma unroll
+                    for (int c = 0; c < RL; ++c) sacc[i] = fmaf(y[0][c], z[c * 32], sacc[i]);
+                } else {
+                    const float *x = v + pb[i] * RL * 32 + lane, *z = v + pb2[i] * RL * 32 + lane;
+#pragma unroll
+                    for (int c = 0; c < RL; ++c) sacc[i] = fmaf(x[c * 32], z[c * 32], sacc[i]);
+                }
+            }
+        } else {
+            (void)v;
         }
     };
     issue(0);
@@ -494,7 +536,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     for (int p = 0; p <= PW; ++p) {
         cp_async_wait<1>();  // period p has landed
         bsync();             // ... for every thread's copies; period p-1's buffer is free
-        if (FUSED && *fw->abort) {  // read by every thread after the same barrier
+        if (WAITS && *fw->abort) {  // read by every thread after the same barrier
             aborted = true;
             break;
         }
@@ -519,10 +561,23 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
         }
     }
     cp_async_wait<0>();
-    if (FUSED)
+    if (FUSED) {
         fused_barrier_all<NT>();  // the band warp is done too, bandres is final
-    else
+    } else if (WAITS) {           // the band CTA's results: wait for its done flag
+        if (threadIdx.x == 0) {
+            int spins = 0;
+            while (*fw->done == 0 && ++spins < fw->limit) __nanosleep(64);
+            if (*fw->done == 0) {
+                *fw->abort = 1;
+                atomicOr(fw->status, kStatusTimeout);
+            }
+            __threadfence();
+        }
         __syncthreads();
+        aborted = aborted || *fw->abort;
+    } else {
+        __syncthreads();
+    }
     if (aborted) {
         if (tb < 32) binfo[lane] = kInfoTimeout;
         return;
@@ -532,11 +587,18 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     // block factors C = A22 - S = L22 L22^T in FP64
     float *sS = stage;  // the staging is free now
     bsync();
+    if constexpr (REG) {
 #pragma unroll
-    for (int i = 0; i < NPC; ++i)
-        if (i < npw) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+        for (int b = 0; b < W; ++b)
+#pragma unroll
+            for (int b2 = 0; b2 <= b; ++b2) sS[(lane * W + b) * W + b2] = sacc[b * (b + 1) / 2 + b2];
+    } else {
+#pragma unroll
+        for (int i = 0; i < NPC; ++i)
+            if (i < npw) sS[(lane * W + pb[i]) * W + pb2[i]] = sacc[i];
+    }
     bsync();
-    const bool live_end = FUSED ? (live && fw->bandres[lane] == 0) : live;
+    const bool live_end = WAITS ? (live && ((volatile const int *)fw->bandres)[lane] == 0) : live;
     if (tb < 32 && live_end) {
         double *C = reinterpret_cast<double *>(stage + 32 * 16 * 16) + lane * (W * W + 1);  // odd stride
         double *outp = const_cast<double *>(out);
@@ -565,7 +627,7 @@ __device__ __forceinline__ void f32_border(const F32Slice &sl, const float *__re
     }
 }
 
-template <int W, int WMIN, int NT, bool FUSED = false>
+template <int W, int WMIN, int NT, int FUSED = kBorderAfter>
 struct F32BorderDispatch {
     __device__ static void run(int w, const F32Slice &sl, const float *shs, float *l21, const double *out,
                                const int64_t *s_off, const int *s_n, const int *s_live, float *stage, int *binfo,
@@ -577,7 +639,7 @@ struct F32BorderDispatch {
         F32BorderDispatch<W - 1, WMIN, NT, FUSED>::run(w, sl, shs, l21, out, s_off, s_n, s_live, stage, binfo, fw);
     }
 };
-template <int WMIN, int NT, bool FUSED>
+template <int WMIN, int NT, int FUSED>
 struct F32BorderDispatch<WMIN - 1, WMIN, NT, FUSED> {
     __device__ static void run(int, const F32Slice &, const float *, float *, const double *, const int64_t *,
                                const int *, const int *, float *, int *, const FusedWait * = nullptr) {}
@@ -648,6 +710,16 @@ void launch_band_groups(sympix_plan_t pl, double *blocks, int32_t *info, cudaStr
 // hi_only: only the slices with w > 12 (the narrow-band kernel has the rest)
 void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only);
 void launch_f32_fused(sympix_plan_t pl, int nf, double *blocks, int32_t *info, cudaStream_t st);
+// band and border passes of the w <= 8 slices in two CTAs of one
+// cooperative launch per slice (sympix_factor_split.cu), and whether that
+// launch's CTAs can all be resident at once
+bool f32_split_fits(sympix_plan_t pl);
+void launch_f32_split_w8(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+
+// the border rows and corners of the fused-range slices by column chunks,
+// after their band pass (sympix_l21.cu); hi_only: only the slices with
+// 9 <= w <= 12, everything on `st`, no trace marks
+void launch_f32_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only = false);
 constexpr int kDefaultWaitLimit = 1 << 22;  // polls of a bounded device wait (about 0.3 s)
 void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,
                               cudaStream_t st);

@@ -27,6 +27,14 @@ int cuda_error(cudaError_t e, const char *what);
 // Record a trace event on `st` (no-op unless the plan traces and `st` is not
 // capturing); `name` labels the span since the previous mark, null starts a call.
 void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
+// columns per chunk of the chunked border solve for width w, and the floats
+// of its per-item scratch (a W x W matrix, the corner sums) for 32 lanes
+int l21_chunk_cols_host(int w);
+int l21_mat_floats();
+int l21_pair_floats();
+// whether the split FP32 launch of a plan's w <= 8 slices can have every CTA
+// resident at once (sympix_factor_split.cu)
+bool f32_split_fits(sympix_plan_t pl);
 
 // Widest band of the narrow-band factor (k_pband_chol), and the elements of
 // one tile of its FP32 commit.
@@ -240,6 +248,23 @@ struct sympix_plan_s {
     std::vector<int2> f32_tiles;  // (slice, first element) of the band shadow transposes
     std::vector<int2> f32_out_tiles;  // the same, then (slice, -1 - first element) of L21
     int f32_slices_fused = 0;     // slices with w <= 12, band and border fused (they come first)
+    int f32_slices_w8 = 0;        // of those, the slices with w <= 8 (they come first)
+    // border rows of the fused-range slices by column chunks: work items
+    // (slice, chunk) with each slice's chunks consecutive, the slices with
+    // w >= 1, each slice's first item and chunk count, and per item the
+    // W x W transfer, particular and start windows and the corner sums
+    std::vector<int2> l21_items;
+    std::vector<int32_t> l21_slices, l21_first, l21_nch;
+    int l21_items_w8 = 0;   // items of slices with w <= 8 (they come first)
+    int l21_slices_w8 = 0;  // entries of l21_slices with w <= 8 (they come first)
+    sympix::DevBuf<int2> d_l21_items;
+    sympix::DevBuf<int32_t> d_l21_slices, d_l21_first, d_l21_nch;
+    sympix::DevBuf<float> d_l21_T, d_l21_P, d_l21_S, d_l21_C;
+    // the split FP32 factor: per fused-range slice a progress and a done word
+    // (zero between launches) and the band passes' results
+    sympix::DevBuf<int> d_split_flags, d_split_bandres;
+    cudaStream_t f32_side = nullptr;  // the fused 9 <= w <= 12 slices beside the w <= 8 ones
+    cudaEvent_t f32_fork = nullptr, f32_join = nullptr;
     // the f32 transposes of slices with w > 12 only (the narrow-band factor
     // covers w <= 12 unless the two-role fused kernel is selected)
     std::vector<int2> f32_tiles_hi, f32_out_tiles_hi;
@@ -262,9 +287,11 @@ struct sympix_plan_s {
     cudaEvent_t chol_side_join = nullptr;
     // kernel for periodic bands w <= 12, per factor arithmetic (SYMPIX_PREC_*):
     // 0 k_pband_chol (G lanes per block), 1 the earlier kernels (FP32: the
-    // two-role kernel on an FP32 band copy; FP64 / split FP32: lane groups).
-    // Defaults from measurement at l_max = 3000: FP64 0, FP32 1, split FP32 1.
-    int narrow_pref[3] = {0, 1, 1};
+    // two-role kernel on an FP32 band copy; FP64 / split FP32: lane groups),
+    // 2 (FP32) band pass and chunked border solve, 3 (FP32) band and border
+    // CTAs of one cooperative launch for w <= 8, 2 for 9 <= w <= 12.
+    // Defaults from measurement at l_max = 3000: FP64 0, FP32 3, split FP32 1.
+    int narrow_pref[3] = {0, 3, 1};
     int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;
@@ -315,6 +342,9 @@ struct sympix_plan_s {
         if (chol_fork) cudaEventDestroy(chol_fork);
         if (chol_side) cudaStreamDestroy(chol_side);
         if (chol_side_join) cudaEventDestroy(chol_side_join);
+        if (f32_side) cudaStreamDestroy(f32_side);
+        if (f32_fork) cudaEventDestroy(f32_fork);
+        if (f32_join) cudaEventDestroy(f32_join);
     }
     double fp32_pivot_floor = 0.05;  // FP32 factor: rescue in FP64 below this pivot ratio
     // device status word (bit 1: a bounded wait ran out), read and cleared by

@@ -325,6 +325,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             }
             bd.format = (wrap || 2 * w + 1 >= bd.n || w > 64) ? SYMPIX_BLOCK_DENSE : SYMPIX_BLOCK_PBAND;
             const int64_t n = bd.n;
+            // every block starts on a 32-byte boundary (a DRAM sector)
+            offp = (offp + 3) & ~int64_t(3);
+            offd = (offd + 3) & ~int64_t(3);
             bd.off_pband = offp;
             bd.off_dense = offd;
             if (bd.format == SYMPIX_BLOCK_PBAND) {
@@ -463,6 +466,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                     if (w > 12) tiles21_hi.push_back(make_int2(idx, (int)(-1 - e0)));
                 }
                 if (w <= 12) ++pl->f32_slices_fused;
+                if (w <= 8) ++pl->f32_slices_w8;
                 pl->f32_slices.push_back(sl);
             }
         }
@@ -475,6 +479,11 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     }
     if (cudaEventCreateWithFlags(&pl->chol_fork, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_error(SYMPIX_ECUDA, "sympix_support: event of the narrow-band factor"));
+    if (pl->f32_slices_w8 > 0 && pl->f32_slices_fused > pl->f32_slices_w8 &&
+        (cudaStreamCreateWithFlags(&pl->f32_side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&pl->f32_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&pl->f32_join, cudaEventDisableTiming) != cudaSuccess))
+        return fail(set_error(SYMPIX_ECUDA, "sympix_support: stream of the FP32 factor"));
     if ((!pl->factor_items[1].empty() || !pl->factor_items[2].empty()) &&
         (cudaStreamCreateWithFlags(&pl->chol_side, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreateWithFlags(&pl->chol_side_join, cudaEventDisableTiming) != cudaSuccess))
@@ -511,6 +520,37 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                 for (int64_t e0 = 0; e0 < lim; e0 += kCommitTileElems) pl->chol_tiles.push_back(make_int2(b, (int)e0));
             }
         }
+    }
+    // chunked border solve of the fused-range slices (1 <= w <= 12)
+    pl->l21_first.assign(pl->f32_slices_fused, -1);
+    pl->l21_nch.assign(pl->f32_slices_fused, 0);
+    for (int si = 0; si < pl->f32_slices_fused; ++si) {
+        const F32Slice &sl = pl->f32_slices[si];
+        const int kc = sl.rows - sl.w;
+        if (sl.w < 1 || kc <= 0) continue;
+        const int cols = l21_chunk_cols_host(sl.w), nch = (kc + cols - 1) / cols;
+        pl->l21_slices.push_back(si);
+        pl->l21_first[si] = (int32_t)pl->l21_items.size();
+        pl->l21_nch[si] = nch;
+        for (int q = 0; q < nch; ++q) pl->l21_items.push_back(make_int2(si, q));
+        if (sl.w <= 8) {
+            pl->l21_items_w8 = (int)pl->l21_items.size();
+            pl->l21_slices_w8 = (int)pl->l21_slices.size();
+        }
+    }
+    if (!pl->l21_items.empty()) {
+        const int64_t ni = (int64_t)pl->l21_items.size();
+        if ((rc = pl->d_l21_items.upload(pl->l21_items)) || (rc = pl->d_l21_slices.upload(pl->l21_slices)) ||
+            (rc = pl->d_l21_first.upload(pl->l21_first)) || (rc = pl->d_l21_nch.upload(pl->l21_nch)) ||
+            (rc = pl->d_l21_T.alloc(ni * l21_mat_floats())) || (rc = pl->d_l21_P.alloc(ni * l21_mat_floats())) ||
+            (rc = pl->d_l21_S.alloc(ni * l21_mat_floats())) || (rc = pl->d_l21_C.alloc(ni * l21_pair_floats())))
+            return fail(rc);
+    }
+    if (pl->f32_slices_fused > 0) {
+        if ((rc = pl->d_split_flags.alloc(2 * (int64_t)pl->f32_slices_fused)) ||
+            (rc = pl->d_split_bandres.alloc(32 * (int64_t)pl->f32_slices_fused)))
+            return fail(rc);
+        SPX_CUDA(cudaMemset(pl->d_split_flags.p, 0, 2 * sizeof(int) * pl->f32_slices_fused));
     }
     if ((rc = pl->d_f32_items.upload(pl->f32_items)) || (rc = pl->d_f32_slices.upload(pl->f32_slices)) ||
         (rc = pl->d_f32_tiles.upload(pl->f32_tiles)) || (rc = pl->d_f32_out_tiles.upload(pl->f32_out_tiles)) ||
@@ -572,11 +612,15 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         return SYMPIX_OK;
     }
     if (option == SYMPIX_OPT_NARROW_FACTOR) {
-        if (value != 0.0 && value != 1.0 && value != -1.0)
-            return set_error(SYMPIX_EINVAL, "sympix_plan_option: narrow factor kernel is -1, 0 or 1");
+        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != -1.0)
+            return set_error(SYMPIX_EINVAL, "sympix_plan_option: narrow factor kernel is -1, 0, 1, 2 or 3");
         if (value == -1.0) {
             pl->narrow_pref[SYMPIX_PREC_FP64] = 0;
-            pl->narrow_pref[SYMPIX_PREC_FP32] = 1;
+            pl->narrow_pref[SYMPIX_PREC_FP32] = 3;
+            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
+        } else if (value == 2.0 || value == 3.0) {  // the chunked border solve and the split kernel: FP32 only
+            pl->narrow_pref[SYMPIX_PREC_FP64] = 1;
+            pl->narrow_pref[SYMPIX_PREC_FP32] = (int)value;
             pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
         } else {
             for (int &v : pl->narrow_pref) v = (int)value;
@@ -665,7 +709,8 @@ extern "C" int sympix_autotune(sympix_plan_t pl, const double *bl, const double 
         factor_precision <= 2) {
         best = 1e30f;
         int best_k = pl->narrow_pref[factor_precision];
-        for (int kk : {0, 1}) {
+        for (int kk : {0, 1, 2, 3}) {
+            if (kk >= 2 && factor_precision != SYMPIX_PREC_FP32) continue;
             pl->narrow_pref[factor_precision] = kk;
             float ms = 0.0f;
             auto run = [&] {
@@ -775,10 +820,21 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
             // slices with w > 12: shadow in, band pass, border pass, write-back, FP64 rescue of list 2
             if (nsl > nfu) f += 4 + (l2 ? 1 : 0);
         } else if (nsl > 0) {
-            // shadow in, the fused kernel (w <= 12), band and border passes, FP64
-            // write-back, then the FP64 rescue launches (which return at once
-            // for blocks that need none)
-            f += 2 + (nfu > 0 ? 1 : 0) + (nsl > nfu ? 2 : 0);
+            // shadow in, the fused kernels (w <= 8 and 9 <= w <= 12), band and
+            // border passes, FP64 write-back, then the FP64 rescue launches
+            // (which return at once for blocks that need none)
+            const int n8 = pl->f32_slices_w8;
+            const int nhi_items = (int)pl->l21_items.size() - pl->l21_items_w8;
+            if (pl->narrow_pref[SYMPIX_PREC_FP32] == 3 && f32_split_fits(pl))
+                // the split launch (w <= 8); band pass and the five chunked kernels of 9 <= w <= 12
+                f += 2 + (n8 > 0 ? 1 : 0) + (nfu > n8 ? 1 + (nhi_items > 0 ? 5 : 0) : 0) + (nsl > nfu ? 2 : 0);
+            else if (pl->narrow_pref[SYMPIX_PREC_FP32] == 2)  // band pass, then transfer, carry, solve, corner sums, corners
+                f += 2 + (nfu > 0 ? 1 : 0) + (nsl > nfu ? 2 : 0) +
+                     (pl->l21_items.empty() ? 0
+                                            : 2 + 2 * (pl->l21_items_w8 > 0 ? 1 : 0) +
+                                                  3 * ((int)pl->l21_items.size() > pl->l21_items_w8 ? 1 : 0));
+            else
+                f += 2 + (n8 > 0 ? 1 : 0) + (nfu > n8 ? 1 : 0) + (nsl > nfu ? 2 : 0);
             f += (l0 ? 2 : 0) + (l1 ? 1 : 0) + (l2 ? 1 : 0);
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
@@ -848,7 +904,10 @@ extern "C" int sympix_plan_device_bytes(sympix_plan_t pl, size_t *bytes, size_t 
                pl->d_l21_il.bytes() + pl->d_f32_out_tiles.bytes() + pl->d_shadow.bytes() + pl->d_chol_items.bytes() +
                pl->d_chol_sl32.bytes() + pl->d_chol_sl64.bytes() + pl->d_chol_tiles.bytes() +
                pl->d_f32_tiles_hi.bytes() + pl->d_f32_out_tiles_hi.bytes() + pl->d_status.bytes() +
-               pl->d_ring_off.bytes() + pl->d_ring_stride.bytes();
+               pl->d_ring_off.bytes() + pl->d_ring_stride.bytes() + pl->d_l21_items.bytes() +
+               pl->d_l21_slices.bytes() + pl->d_l21_first.bytes() + pl->d_l21_nch.bytes() + pl->d_l21_T.bytes() +
+               pl->d_l21_P.bytes() + pl->d_l21_S.bytes() + pl->d_l21_C.bytes() + pl->d_split_flags.bytes() +
+               pl->d_split_bandres.bytes();
     for (const auto &kv : pl->coupling) b += kv.second.d_desc.bytes();
     for (int i = 0; i < 5; ++i) b += pl->d_items_pband[i].bytes();
     for (int i = 0; i < 6; ++i) b += pl->d_factor_items[i].bytes();

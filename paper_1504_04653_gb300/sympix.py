@@ -217,7 +217,7 @@ class Plan:
         return a.value, b.value
 
     def narrow_kernels(self):
-        """{arithmetic: 0 (G-lane kernel) or 1 (earlier kernels)} for w <= 12 bands."""
+        """{arithmetic: 0 (G-lane), 1 (earlier kernels), 2 (FP32 chunked border) or 3 (FP32 split CTAs)}."""
         nk = (ctypes.c_int * 3)()
         _check(lib().sympix_plan_tuning(self._h, None, None, nk))
         return {"fp64": nk[0], "fp32": nk[1], "fp32x2": nk[2]}
@@ -231,7 +231,9 @@ class Plan:
         return self.tuning()
 
     def set_narrow_factor(self, kernel: int):
-        """w <= 12 bands: 0 the G-lane kernel, 1 the earlier kernels, -1 per arithmetic (default)."""
+        """w <= 12 bands: 0 the G-lane kernel, 1 the earlier kernels, 2 (FP32) the band pass and the
+        border rows by column chunks, 3 (FP32) band and border passes in two CTAs of one cooperative
+        launch, -1 per arithmetic (default)."""
         _check(lib().sympix_plan_option(self._h, OPT_NARROW_FACTOR, float(kernel)))
 
     def set_wait_limit(self, polls: int):

@@ -683,7 +683,7 @@ def test_chunked_tables(S, dev, nops):
 
 # -- the narrow-band factor (w <= 12): every width, every arithmetic ------------
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("fprec", ["fp64", "fp32", "fp32x2"])
 def test_narrow_factor_every_width(S, dev, fprec, kernel):
     """Operators whose radii give periodic-band widths from 0 to 12 at
@@ -747,7 +747,7 @@ def test_narrow_factor_matches_earlier_kernels(S, dev, fprec):
     plan.set_narrow_factor(1)
     ib = S.sympix_factor_blocks(plan, b, precision=fprec).cpu().numpy()
     plan.set_narrow_factor(-1)
-    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 1, "fp32x2": 1}
+    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 3, "fp32x2": 1}
     assert np.array_equal(ia, ib) and np.all(ia == 0)
     A, B = a.cpu().numpy(), b.cpu().numpy()
     tol = {"fp64": 1e-13, "fp32x2": 1e-11, "fp32": 1e-5}[fprec]
@@ -755,6 +755,89 @@ def test_narrow_factor_matches_earlier_kernels(S, dev, fprec):
         La = S.unpack_block(A, plan, "pband", 0, j, factored=True)
         Lb = S.unpack_block(B, plan, "pband", 0, j, factored=True)
         assert _err(La, Lb) <= tol, (j, _err(La, Lb))
+
+
+def _fp32_factors(S, dev, wl, kernels, rings):
+    import torch
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(wl.ninv(colat), device=dev), precision="fp32")
+    out = {}
+    for k in kernels:
+        b = blocks.clone()
+        plan.set_narrow_factor(k)
+        info = S.sympix_factor_blocks(plan, b, precision="fp32").cpu().numpy()
+        h = b.cpu().numpy()
+        out[k] = (info, {j: S.unpack_block(h, plan, "pband", 0, j, factored=True) for j in rings})
+        del b
+    return plan, blocks, out
+
+
+def test_chunked_border_matches_column_sweep_lmax500(S, dev):
+    """FP32 option 2 (the band pass, then the border rows solved by column
+    chunks with exact carries) and option 3 (band and border passes in two
+    CTAs of one cooperative launch) against option 1 (the border swept column
+    by column behind the band in the same CTA): the same factor within FP32
+    rounding, the same pivot verdicts, on rings long enough for several
+    chunks (and so the carry between them)."""
+    wl = W.WORKLOADS["lmax500"]
+    rings = list(range(0, 501, 25)) + [249, 250, 251]
+    plan, _, out = _fp32_factors(S, dev, wl, (1, 2, 3), rings)
+    assert np.array_equal(out[1][0], out[2][0]) and np.all(out[1][0] == 0)
+    assert np.array_equal(out[1][0], out[3][0])
+    for j in rings:
+        assert _err(out[3][1][j], out[1][1][j]) <= 1e-5, j
+    nchunks = 0
+    for j in rings:
+        _, n, w, fmt = plan.block_layout("pband", 0, j)
+        if fmt == S.BLOCK_PBAND:
+            nchunks = max(nchunks, -(-(n - w) // ((288 // (w + 1)) * (w + 1))))
+        assert _err(out[2][1][j], out[1][1][j]) <= 1e-5, (j, n, w, _err(out[2][1][j], out[1][1][j]))
+    assert nchunks >= 3
+
+
+def test_chunked_border_matches_column_sweep_lmax3000(S, dev):
+    """The same at full size: the equatorial rings (n = 6075, 22 chunks of
+    288 columns), the w = 10 rings where the ring count changes, and polar
+    and mid-latitude rings."""
+    wl = W.WORKLOADS["lmax3000"]
+    rings = [0, 5, 300, 901, 902, 1500, 2098, 2293, 2700, 3000]
+    plan, _, out = _fp32_factors(S, dev, wl, (1, 2, 3), rings)
+    assert np.array_equal(out[1][0], out[2][0]) and np.array_equal(out[1][0], out[3][0])
+    for j in rings:
+        assert _err(out[3][1][j], out[1][1][j]) <= 1e-5, j
+    widths = set()
+    for j in rings:
+        _, n, w, fmt = plan.block_layout("pband", 0, j)
+        widths.add(int(w))
+        assert _err(out[2][1][j], out[1][1][j]) <= 1e-5, (j, n, w, _err(out[2][1][j], out[1][1][j]))
+    assert {8, 9, 10} <= widths
+
+
+def test_chunked_border_rescue_restores_fp64(S, dev):
+    """Option 2 with the pivot floor at 2: every block is sent to the FP64
+    rescue, and the result is the FP64 factor (FP64 accuracy)."""
+    import torch
+    wl = W.WORKLOADS["lmax500"]
+    grid = S.Grid(wl.lmax)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device=dev), torch.tensor(wl.priors(), device=dev))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(wl.ninv(colat), device=dev), precision="fp64")
+    a, b = blocks.clone(), blocks.clone()
+    plan.set_narrow_factor(2)
+    plan.set_pivot_floor(2.0)
+    ia = S.sympix_factor_blocks(plan, a, precision="fp32").cpu().numpy()
+    plan.set_pivot_floor(0.05)
+    ib = S.sympix_factor_blocks(plan, b, precision="fp64").cpu().numpy()
+    assert np.all(ia == 0) and np.all(ib == 0)
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    for j in range(0, grid.nrings, 5):
+        La = S.unpack_block(A, plan, "pband", 0, j, factored=True)
+        Lb = S.unpack_block(B, plan, "pband", 0, j, factored=True)
+        assert _err(La, Lb) <= 1e-12, j
 
 
 def test_narrow_factor_fp32_rescue_restores_fp64(S, dev):

@@ -70,13 +70,16 @@ def test_step_wide_bands_match_direct_calls(storage, fprec):
     assert np.array_equal(info.cpu().numpy(), i_ref)
 
 
-@pytest.mark.parametrize("name,storage,sprec,fprec", [
-    ("lmax500", "pband", "fp32", "fp32"),
-    ("lmax500", "pband", "fp64", "fp64"),
-    ("lmax64", "dense", "fp32x2", "fp32x2"),
+@pytest.mark.parametrize("name,storage,sprec,fprec,narrow", [
+    ("lmax500", "pband", "fp32", "fp32", -1),
+    ("lmax500", "pband", "fp32", "fp32", 2),
+    ("lmax500", "pband", "fp32", "fp32", 3),
+    ("lmax500", "pband", "fp64", "fp64", -1),
+    ("lmax64", "dense", "fp32x2", "fp32x2", -1),
 ])
-def test_step_matches_direct_calls(name, storage, sprec, fprec):
+def test_step_matches_direct_calls(name, storage, sprec, fprec, narrow):
     wl, grid, plan, colat, bl, dl, ninv = _setup(name)
+    plan.set_narrow_factor(narrow)
     s_ref, f_ref, i_ref = _direct(plan, bl, dl, ninv, storage, sprec, fprec)
     nbytes, _ = plan.blocks_size(storage)
     blocks = torch.zeros(nbytes // 8, dtype=torch.float64, device="cuda")
@@ -151,6 +154,18 @@ def test_trace_names_every_kernel():
     S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp32"), precision="fp32")
     names = [n for n, _ in plan.trace_read()]
     for k in ("k_f32_shadow_in", "k_f32_fused", "k_f32_out", "k_factor_rescue"):
+        assert k in names, names
+    # the band pass and the border rows by column chunks
+    plan.set_narrow_factor(2)
+    S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp32"), precision="fp32")
+    names = [n for n, _ in plan.trace_read()]
+    for k in ("k_f32_band_pass", "k_l21_transfer", "k_l21_carry", "k_l21_solve", "k_l21_corner", "k_f32_out"):
+        assert k in names, names
+    # band and border passes in two CTAs of one launch
+    plan.set_narrow_factor(3)
+    S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp32"), precision="fp32")
+    names = [n for n, _ in plan.trace_read()]
+    for k in ("k_f32_shadow_in", "k_f32_split", "k_f32_out"):
         assert k in names, names
     plan.set_narrow_factor(-1)
     assert plan.trace_read() == []
