@@ -152,12 +152,14 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           blocks, G lanes per block sharing the band window; 1 the
                                           earlier kernels (FP32: one lane per block on an FP32
                                           band copy, a band warp and border warps per CTA; FP64 /
-                                          split FP32: lane groups); 2 FP32: the band pass alone,
-                                          then the border rows solved in parallel over column
-                                          chunks; 3 FP32: for w <= 8 band and border passes in two
-                                          CTAs of one cooperative launch (the kernel of 1 where
-                                          they cannot all be resident), 9 <= w <= 12 as 2 beside
-                                          it (2, 3: FP64 / split FP32 as 1); -1 (default) per
+                                          split FP32: lane groups); 2 FP32 and FP64: the band
+                                          pass alone (one lane per block on a band copy of the
+                                          arithmetic), then the border rows solved in parallel
+                                          over column chunks; 3 FP32: for w <= 8 band and border
+                                          passes in two CTAs of one cooperative launch (the
+                                          kernel of 1 where they cannot all be resident),
+                                          9 <= w <= 12 as 2 beside it (3: FP64 as 2; 2, 3: split
+                                          FP32 as 1); -1 (default) per
                                           arithmetic, as measured at l_max 3000: FP64 0, FP32 3,
                                           split FP32 1.  sympix_autotune times the candidates for
                                           its factor arithmetic */

@@ -5,13 +5,16 @@
 
 namespace sympix {
 
-// One CTA per kTileE elements x 32 blocks of a slice.
+// One CTA per kTileE elements x 32 blocks of a slice; V = float (the FP32
+// factor's shadow) or double (the FP64 one).
+template <class V>
 __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ tiles,
                                                        const F32Slice *__restrict__ slices,
                                                        const int32_t *__restrict__ items,
                                                        const BlockDesc *__restrict__ blocks,
-                                                       const double *__restrict__ out, float *__restrict__ sh) {
-    __shared__ float tile[kTileE][33];
+                                                       const double *__restrict__ out, V *__restrict__ sh) {
+    constexpr int P16 = 16 / (int)sizeof(V);  // lanes per 16-byte shadow access
+    __shared__ V tile[kTileE][33];
     __shared__ int64_t s_off[32];
     __shared__ int s_cnt[32];
     const int2 tl = tiles[blockIdx.x];
@@ -34,28 +37,26 @@ __global__ void __launch_bounds__(256) k_f32_shadow_in(const int2 *__restrict__ 
 #pragma unroll
     for (int i = threadIdx.x; i < 16 * kTileE; i += 256) {
         const int L = i / (kTileE / 2), e = 2 * (i % (kTileE / 2));
-        float v0 = 0.0f, v1 = 0.0f;
+        V v0 = V(0), v1 = V(0);
         const int cnt = s_cnt[L];
         if (e0 + e + 1 < cnt) {
             const double2 d = *reinterpret_cast<const double2 *>(out + s_off[L] + e0 + e);
-            v0 = f64_to_f32_bits(d.x);
-            v1 = f64_to_f32_bits(d.y);
+            v0 = elem_from_f64<V>(d.x);
+            v1 = elem_from_f64<V>(d.y);
         } else if (e0 + e < cnt) {
-            v0 = f64_to_f32_bits(out[s_off[L] + e0 + e]);
+            v0 = elem_from_f64<V>(out[s_off[L] + e0 + e]);
         }
         tile[e][L] = v0;
         tile[e + 1][L] = v1;
     }
     __syncthreads();
-    // shadow side: four consecutive blocks of one element per thread
+    // shadow side: P16 consecutive blocks of one element per thread
     const int lim = sl.rows * RL;
-    float *dst = sh + sl.sh + (int64_t)e0 * 32;
+    V *dst = sh + sl.sh + (int64_t)e0 * 32;
 #pragma unroll
-    for (int i = threadIdx.x; i < 8 * kTileE; i += 256) {
-        const int e = i >> 3, L = 4 * (i & 7);
-        if (e0 + e < lim)
-            *reinterpret_cast<float4 *>(dst + e * 32 + L) =
-                make_float4(tile[e][L], tile[e][L + 1], tile[e][L + 2], tile[e][L + 3]);
+    for (int i = threadIdx.x; i < (32 / P16) * kTileE; i += 256) {
+        const int e = i / (32 / P16), L = P16 * (i % (32 / P16));
+        if (e0 + e < lim) store16(dst + e * 32 + L, &tile[e][L]);
     }
 }
 
@@ -76,16 +77,38 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict
     if (bi >= 0) info[bi] = r;
 }
 
+// FP64 band pass on the FP64 shadow, widths up to 12: one warp per slice,
+// one lane per block; info = i + 1 for the first row whose pivot is not
+// positive (the border kernels then leave the block alone).
+__global__ void __launch_bounds__(32) k_f64_band_pass(const F32Slice *__restrict__ slices,
+                                                      const int32_t *__restrict__ items,
+                                                      const BlockDesc *__restrict__ blocks, double *__restrict__ sh,
+                                                      int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) unsigned char f64_smem[];
+    double *stage = reinterpret_cast<double *>(f64_smem);
+    const F32Slice sl = slices[blockIdx.x];
+    const int lane = threadIdx.x;
+    int m = 0, bi = -1;
+    if (lane < sl.count) {
+        bi = items[sl.first + lane];
+        m = blocks[bi].n - sl.w;
+    }
+    const int r = F32BandDispatch<12, double>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, stage, 0.0f);
+    if (bi >= 0) info[bi] = r;
+}
+
 // The factor back to the FP64 blocks: L11 rows from the band shadow and
 // L21 rows from the border buffer, 64 elements x 32 blocks per CTA, through
 // a shared-memory transpose (coalesced on both sides).  Blocks sent to the
-// FP64 rescue are skipped.
+// FP64 rescue are skipped.  V: the shadow's element (float or double).
+template <class V>
 __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles, const F32Slice *__restrict__ slices,
                                                  const int32_t *__restrict__ items,
                                                  const BlockDesc *__restrict__ blocks,
-                                                 const int32_t *__restrict__ info, const float *__restrict__ sh,
-                                                 const float *__restrict__ l21, double *__restrict__ out) {
-    __shared__ float tile[kTileE][33];
+                                                 const int32_t *__restrict__ info, const V *__restrict__ sh,
+                                                 const V *__restrict__ l21, double *__restrict__ out) {
+    constexpr int P16 = 16 / (int)sizeof(V);  // lanes per 16-byte shadow access
+    __shared__ V tile[kTileE][33];
     __shared__ int64_t s_off[32];
     __shared__ int s_n[32], s_live[32];
     const int2 tl = tiles[blockIdx.x];
@@ -110,17 +133,17 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
     }
     const int kc = sl.rows - W;
     const int lim = part21 ? W * kc : sl.rows * RL;
-    const float *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
-    // shadow side: four consecutive blocks of one element per thread
+    const V *src = (part21 ? l21 + sl.l21 : sh + sl.sh) + (int64_t)e0 * 32;
+    // shadow side: P16 consecutive blocks of one element per thread
 #pragma unroll
-    for (int i = threadIdx.x; i < 8 * kTileE; i += 256) {
-        const int e = i >> 3, L = 4 * (i & 7);
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (e0 + e < lim) v = *reinterpret_cast<const float4 *>(src + e * 32 + L);
-        tile[e][L] = v.x;
-        tile[e][L + 1] = v.y;
-        tile[e][L + 2] = v.z;
-        tile[e][L + 3] = v.w;
+    for (int i = threadIdx.x; i < (32 / P16) * kTileE; i += 256) {
+        const int e = i / (32 / P16), L = P16 * (i % (32 / P16));
+        V v[P16];
+#pragma unroll
+        for (int u = 0; u < P16; ++u) v[u] = V(0);
+        if (e0 + e < lim) load16(src + e * 32 + L, v);
+#pragma unroll
+        for (int u = 0; u < P16; ++u) tile[e][L + u] = v[u];
     }
     __syncthreads();
     // FP64 side: two consecutive elements of one block per thread; their
@@ -143,11 +166,10 @@ __global__ void __launch_bounds__(256) k_f32_out(const int2 *__restrict__ tiles,
         const int64_t d0 = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q0 * n + r0 : s_off[L] + ee;
         const int64_t d1 = part21 ? s_off[L] + (int64_t)n * RL + (int64_t)q1 * n + r1 : s_off[L] + ee + 1;
         if (ok0 && ok1 && d1 == d0 + 1 && (d0 & 1) == 0) {
-            *reinterpret_cast<double2 *>(out + d0) =
-                make_double2(f32_to_f64_bits(tile[e][L]), f32_to_f64_bits(tile[e + 1][L]));
+            *reinterpret_cast<double2 *>(out + d0) = make_double2(elem_to_f64(tile[e][L]), elem_to_f64(tile[e + 1][L]));
         } else {
-            if (ok0) out[d0] = f32_to_f64_bits(tile[e][L]);
-            if (ok1) out[d1] = f32_to_f64_bits(tile[e + 1][L]);
+            if (ok0) out[d0] = elem_to_f64(tile[e][L]);
+            if (ok1) out[d1] = elem_to_f64(tile[e + 1][L]);
         }
     }
 }
@@ -161,7 +183,7 @@ void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStre
     const size_t nout = hi_only ? pl->f32_out_tiles_hi.size() : pl->f32_out_tiles.size();
     const int2 *tin = hi_only ? pl->d_f32_tiles_hi.p : pl->d_f32_tiles.p;
     const int2 *tout = hi_only ? pl->d_f32_out_tiles_hi.p : pl->d_f32_out_tiles.p;
-    k_f32_shadow_in<<<(unsigned)nin, 256, 0, st>>>(tin, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks,
+    k_f32_shadow_in<float><<<(unsigned)nin, 256, 0, st>>>(tin, sl, pl->d_f32_items.p, pl->d_blocks.p, blocks,
                                                    pl->d_shadow_il.p);
     trace_mark(pl, st, "k_f32_shadow_in");
     if (nf > 0 && !hi_only) {
@@ -215,12 +237,39 @@ void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStre
             launch_f32_border<512>(pl, nf, ns - nf, blocks, info, st);
         trace_mark(pl, st, "k_f32_border_pass");
     }
-    k_f32_out<<<(unsigned)nout, 256, 0, st>>>(tout, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
+    k_f32_out<float><<<(unsigned)nout, 256, 0, st>>>(tout, sl, pl->d_f32_items.p, pl->d_blocks.p, info, pl->d_shadow_il.p,
                                              pl->d_l21_il.p, blocks);
     trace_mark(pl, st, "k_f32_out");
     // near-degenerate blocks: FP64 from the untouched FP64 input
     launch_band<ArF64>(pl, false, blocks, info, st, 1, hi_only);
     trace_mark(pl, st, "k_factor_rescue");
+}
+
+// The FP64 factor of the periodic bands up to w = 16 on an FP64 shadow:
+// for w <= 12 the transposes around the one-lane-per-block band pass and the
+// chunked border solve (every FP64 instruction does 32 blocks' work), for
+// 12 < w <= 16 the lane-group kernel.  The shadow and the chunk scratch are
+// the FP32 path's buffers, which the plan sizes for doubles.
+void launch_f64_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    const int nf = pl->f32_slices_fused;
+    const size_t nin = pl->f32_tiles_lo.size(), nout = pl->f32_out_tiles_lo.size();
+    if (nf > 0 && nin > 0) {
+        const F32Slice *sl = pl->d_f32_slices.p;
+        double *sh = reinterpret_cast<double *>(pl->d_shadow_il.p), *l21 = reinterpret_cast<double *>(pl->d_l21_il.p);
+        k_f32_shadow_in<double><<<(unsigned)nin, 256, 0, st>>>(pl->d_f32_tiles_lo.p, sl, pl->d_f32_items.p,
+                                                               pl->d_blocks.p, blocks, sh);
+        trace_mark(pl, st, "k_f32_shadow_in");
+        const size_t smem = (size_t)2 * 13 * 13 * 32 * sizeof(double);
+        cudaFuncSetAttribute(k_f64_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_f64_band_pass<<<(unsigned)nf, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, sh, info);
+        trace_mark(pl, st, "k_f64_band_pass");
+        launch_f64_l21(pl, blocks, info, st);
+        k_f32_out<double><<<(unsigned)nout, 256, 0, st>>>(pl->d_f32_out_tiles_lo.p, sl, pl->d_f32_items.p,
+                                                          pl->d_blocks.p, info, sh, l21, blocks);
+        trace_mark(pl, st, "k_f32_out");
+    }
+    launch_band<ArF64>(pl, false, blocks, info, st, 0, true);  // 12 < w <= 16
+    trace_mark(pl, st, "k_factor_band");
 }
 
 }  // namespace sympix

@@ -160,27 +160,68 @@ struct StaticFor<E, E> {
 // idle lane); mmax: the slice's largest m (every lane runs mmax's periods,
 // so that all take part in the staging); stage: the CTA's two period
 // buffers, laid out like the shadow.
-template <int W>
-__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor,
-                                        volatile int *prog) {
+// T = float: FP32, pivots checked against the floor (a block below it
+// returns kRescue and is refactored in FP64).  T = double: FP64 on an FP64
+// shadow, the return value is LAPACK's info (i + 1 for the first row i whose
+// pivot is not positive; the lane stops there).
+// An element of the FP64 input in a shadow's arithmetic (FP32 on the integer
+// ALU, see sympix_arith.cuh), and back to FP64.
+template <class V>
+__device__ __forceinline__ V elem_from_f64(double x);
+template <>
+__device__ __forceinline__ float elem_from_f64<float>(double x) { return f64_to_f32_bits(x); }
+template <>
+__device__ __forceinline__ double elem_from_f64<double>(double x) { return x; }
+__device__ __forceinline__ double elem_to_f64(float x) { return f32_to_f64_bits(x); }
+__device__ __forceinline__ double elem_to_f64(double x) { return x; }
+// A 16-byte group of consecutive elements (four floats or two doubles).
+__device__ __forceinline__ void store16(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store16(double *p, const double *v) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void load16(const float *p, float *v) {
+    const float4 e = *reinterpret_cast<const float4 *>(p);
+    v[0] = e.x;
+    v[1] = e.y;
+    v[2] = e.z;
+    v[3] = e.w;
+}
+__device__ __forceinline__ void load16(const double *p, double *v) {
+    const double2 e = *reinterpret_cast<const double2 *>(p);
+    v[0] = e.x;
+    v[1] = e.y;
+}
+
+__device__ __forceinline__ float band_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double band_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float band_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double band_fma(double a, double b, double c) { return fma(a, b, c); }
+
+template <class T, int W>
+__device__ __forceinline__ int band_lanes(T *shs, int lane, int m, int mmax, T *stage, float floor,
+                                          volatile int *prog) {
     constexpr int RL = W + 1, CH = RL * RL;
-    float *band = shs + lane;  // element e at band[32 e]
+    constexpr bool F64 = sizeof(T) == 8;
+    constexpr int PER16 = 16 / (int)sizeof(T);  // elements per 16-byte copy
+    T *band = shs + lane;  // element e at band[32 e]
     auto issue = [&](int per) {
         const int r0 = per * RL;
         if (r0 < mmax) {  // rows r0 .. r0 + W < the slice's rows
-            float *dst = stage + (per & 1) * CH * 32;
-            const float *src = shs + (int64_t)r0 * RL * 32;
-            for (int i = lane; i < CH * 8; i += 32) cp_async16(dst + 4 * i, src + 4 * i);
+            T *dst = stage + (per & 1) * CH * 32;
+            const T *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = lane; i < CH * 32 / PER16; i += 32) cp_async16(dst + PER16 * i, src + PER16 * i);
         }
         cp_async_commit();
     };
     issue(1);
-    float Wn[RL][RL];  // [row slot][column slot]
-    float od[RL];      // original diagonal per row slot
+    T Wn[RL][RL];  // [row slot][column slot]
+    T od[RL];      // original diagonal per row slot
 #pragma unroll
     for (int r = 0; r <= W; ++r) {
 #pragma unroll
-        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[((int64_t)r * RL + (r - c)) * 32] : 0.0f;
+        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[((int64_t)r * RL + (r - c)) * 32] : T(0);
         od[r] = Wn[r][r];
     }
     // One elimination step at phase PH (k = p RL + PH).  lrow = band row
@@ -189,19 +230,22 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
     // The pivot d of row k and rs = 1/sqrt(d) arrive from the previous
     // step: each step forms the next pivot first (one product) and starts
     // its rsqrt before the rest of the update.
-    bool bad = !(Wn[0][0] > floor * od[0]);
-    float d = Wn[0][0], rs = rsqrtf(Wn[0][0]);
-    auto step = [&](auto PHc, float *lrow, const float *src, bool live, int kbase) {
+    // FP32: the floor test; FP64: the first non-positive pivot (row + 1)
+    auto fails = [&](T dv, T odv) { return F64 ? !(dv > T(0)) : !(dv > T(floor) * odv); };
+    bool bad = m > 0 && fails(Wn[0][0], od[0]);
+    int info = bad ? 1 : 0;
+    T d = Wn[0][0], rs = band_rsqrt(Wn[0][0]);
+    auto step = [&](auto PHc, T *lrow, const T *src, bool live, int kbase) {
         constexpr int PH = decltype(PHc)::value;
         constexpr int P1 = (PH + 1) % RL;
         if (!live) return;
         lrow[PH * RL * 32] = d * rs;
-        float l[RL];
-        float dn = 0.0f, rsn = 0.0f;
+        T l[RL];
+        T dn = T(0), rsn = T(0);
         if constexpr (W >= 1) {
             l[1] = Wn[P1][PH] * rs;
-            dn = fmaf(-l[1], l[1], Wn[P1][P1]);
-            rsn = rsqrtf(dn);
+            dn = band_fma(-l[1], l[1], Wn[P1][P1]);
+            rsn = band_rsqrt(dn);
         }
 #pragma unroll
         for (int r = 2; r <= W; ++r) l[r] = Wn[(PH + r) % RL][PH] * rs;
@@ -211,7 +255,8 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
         for (int r = 1; r <= W; ++r)
 #pragma unroll
             for (int c = 1; c <= r; ++c)
-                if (r > 1 || c > 1) Wn[(PH + r) % RL][(PH + c) % RL] = fmaf(-l[r], l[c], Wn[(PH + r) % RL][(PH + c) % RL]);
+                if (r > 1 || c > 1)
+                    Wn[(PH + r) % RL][(PH + c) % RL] = band_fma(-l[r], l[c], Wn[(PH + r) % RL][(PH + c) % RL]);
         // row k+1+W enters slot PH at columns k+1 .. k+1+W
 #pragma unroll
         for (int c = 0; c <= W; ++c) Wn[PH][(PH + 1 + c) % RL] = src[(PH * RL + (W - c)) * 32];
@@ -223,18 +268,20 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
             (void)dn;
             (void)rsn;
             d = Wn[0][0];
-            rs = rsqrtf(d);
+            rs = band_rsqrt(d);
         }
         // the next pivot (rows >= m are not A11's); includes d <= 0 and NaN
-        bad |= kbase + PH + 1 < m && !(d > floor * od[P1]);
+        const bool f = kbase + PH + 1 < m && fails(d, od[P1]);
+        if (f && !bad) info = kbase + PH + 2;
+        bad |= f;
     };
     const int PW = mmax / RL;  // the slice's last period
     for (int p = 0; p <= PW; ++p) {
         issue(p + 2);
         cp_async_wait<1>();  // period p + 1 has landed
         __syncwarp();        // ... for every lane's copies
-        const float *src = stage + ((p + 1) & 1) * CH * 32 + lane;
-        float *lrow = band + (int64_t)p * RL * RL * 32;
+        const T *src = stage + ((p + 1) & 1) * CH * 32 + lane;
+        T *lrow = band + (int64_t)p * RL * RL * 32;
         const int left = m - p * RL;  // this lane's steps left
         const int kbase = p * RL;
         if (left >= RL) {
@@ -258,22 +305,31 @@ __device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, f
         __syncwarp();
         if (lane == 0) *prog = 0x7fffffff;
     }
-    return bad ? kRescue : 0;
+    if constexpr (F64)
+        return info;
+    else
+        return bad ? kRescue : 0;
 }
 
 template <int W>
+__device__ __forceinline__ int f32_band(float *shs, int lane, int m, int mmax, float *stage, float floor,
+                                        volatile int *prog) {
+    return band_lanes<float, W>(shs, lane, m, mmax, stage, floor, prog);
+}
+
+template <int W, class T = float>
 struct F32BandDispatch {
-    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage, float floor,
                               volatile int *prog = nullptr) {
-        if (w == W) return f32_band<W>(shs, lane, m, mmax, stage, floor, prog);
-        return F32BandDispatch<W - 1>::run(w, shs, lane, m, mmax, stage, floor, prog);
+        if (w == W) return band_lanes<T, W>(shs, lane, m, mmax, stage, floor, prog);
+        return F32BandDispatch<W - 1, T>::run(w, shs, lane, m, mmax, stage, floor, prog);
     }
 };
-template <>
-struct F32BandDispatch<0> {
-    __device__ static int run(int w, float *shs, int lane, int m, int mmax, float *stage, float floor,
+template <class T>
+struct F32BandDispatch<0, T> {
+    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage, float floor,
                               volatile int *prog = nullptr) {
-        return w == 0 ? f32_band<0>(shs, lane, m, mmax, stage, floor, prog) : -1;
+        return w == 0 ? band_lanes<T, 0>(shs, lane, m, mmax, stage, floor, prog) : -1;
     }
 };
 
@@ -720,6 +776,10 @@ void launch_f32_split_w8(sympix_plan_t pl, double *blocks, int32_t *info, cudaSt
 // after their band pass (sympix_l21.cu); hi_only: only the slices with
 // 9 <= w <= 12, everything on `st`, no trace marks
 void launch_f32_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only = false);
+// the same in FP64 on the FP64 band shadow (every fused-range slice)
+void launch_f64_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+// the FP64 factor of the periodic bands up to w = 16 (sympix_factor_f32.cu)
+void launch_f64_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
 constexpr int kDefaultWaitLimit = 1 << 22;  // polls of a bounded device wait (about 0.3 s)
 void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,
                               cudaStream_t st);

@@ -268,6 +268,8 @@ struct sympix_plan_s {
     // the f32 transposes of slices with w > 12 only (the narrow-band factor
     // covers w <= 12 unless the two-role fused kernel is selected)
     std::vector<int2> f32_tiles_hi, f32_out_tiles_hi;
+    // ... and of slices with w <= 12 only (the FP64 path's shadow)
+    std::vector<int2> f32_tiles_lo, f32_out_tiles_lo;
     int64_t size_shadow_hi = 0, size_l21_hi = 0;  // floats of the w > 12 slices (they come first in the buffers)
     // narrow-band factor (w <= 12, periodic-band storage): blocks by width,
     // most expensive first; slices for FP32 (8 lanes) and for FP64 / split
@@ -318,7 +320,7 @@ struct sympix_plan_s {
     sympix::DevBuf<float> d_shadow;     // FP32 band rows of wide blocks / FP32 L11 of narrow ones, at their pband offsets
     sympix::DevBuf<int32_t> d_chol_items;
     sympix::DevBuf<CholSlice> d_chol_sl32, d_chol_sl64;
-    sympix::DevBuf<int2> d_chol_tiles, d_f32_tiles_hi, d_f32_out_tiles_hi;
+    sympix::DevBuf<int2> d_chol_tiles, d_f32_tiles_hi, d_f32_out_tiles_hi, d_f32_tiles_lo, d_f32_out_tiles_lo;
     bool table_ready = false;
     // blocks between rings: their layouts per ring offset; d evaluated at every
     // class (not only the same-ring ones) once such a layout exists

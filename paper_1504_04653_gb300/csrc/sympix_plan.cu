@@ -443,7 +443,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                     pl->size_l21_hi = l21;
                 }
             }
-        std::vector<int2> tiles21, tiles21_hi;
+        std::vector<int2> tiles21, tiles21_hi, tiles21_lo;
         for (int w = 0; w <= 16; ++w) {
             const int first = (int)pl->f32_items.size(), cnt = (int)byw[w].size();
             pl->f32_items.insert(pl->f32_items.end(), byw[w].begin(), byw[w].end());
@@ -460,10 +460,12 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
                 for (int64_t e0 = 0; e0 < elems; e0 += kTileE) {
                     pl->f32_tiles.push_back(make_int2(idx, (int)e0));
                     if (w > 12) pl->f32_tiles_hi.push_back(make_int2(idx, (int)e0));
+                    else pl->f32_tiles_lo.push_back(make_int2(idx, (int)e0));
                 }
                 for (int64_t e0 = 0; e0 < elems21; e0 += kTileE) {
                     tiles21.push_back(make_int2(idx, (int)(-1 - e0)));
                     if (w > 12) tiles21_hi.push_back(make_int2(idx, (int)(-1 - e0)));
+                    else tiles21_lo.push_back(make_int2(idx, (int)(-1 - e0)));
                 }
                 if (w <= 12) ++pl->f32_slices_fused;
                 if (w <= 8) ++pl->f32_slices_w8;
@@ -476,6 +478,8 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         pl->f32_out_tiles.insert(pl->f32_out_tiles.end(), tiles21.begin(), tiles21.end());
         pl->f32_out_tiles_hi = pl->f32_tiles_hi;
         pl->f32_out_tiles_hi.insert(pl->f32_out_tiles_hi.end(), tiles21_hi.begin(), tiles21_hi.end());
+        pl->f32_out_tiles_lo = pl->f32_tiles_lo;
+        pl->f32_out_tiles_lo.insert(pl->f32_out_tiles_lo.end(), tiles21_lo.begin(), tiles21_lo.end());
     }
     if (cudaEventCreateWithFlags(&pl->chol_fork, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_error(SYMPIX_ECUDA, "sympix_support: event of the narrow-band factor"));
@@ -542,8 +546,8 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         const int64_t ni = (int64_t)pl->l21_items.size();
         if ((rc = pl->d_l21_items.upload(pl->l21_items)) || (rc = pl->d_l21_slices.upload(pl->l21_slices)) ||
             (rc = pl->d_l21_first.upload(pl->l21_first)) || (rc = pl->d_l21_nch.upload(pl->l21_nch)) ||
-            (rc = pl->d_l21_T.alloc(ni * l21_mat_floats())) || (rc = pl->d_l21_P.alloc(ni * l21_mat_floats())) ||
-            (rc = pl->d_l21_S.alloc(ni * l21_mat_floats())) || (rc = pl->d_l21_C.alloc(ni * l21_pair_floats())))
+            (rc = pl->d_l21_T.alloc(2 * ni * l21_mat_floats())) || (rc = pl->d_l21_P.alloc(2 * ni * l21_mat_floats())) ||
+            (rc = pl->d_l21_S.alloc(2 * ni * l21_mat_floats())) || (rc = pl->d_l21_C.alloc(2 * ni * l21_pair_floats())))
             return fail(rc);
     }
     if (pl->f32_slices_fused > 0) {
@@ -556,8 +560,10 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         (rc = pl->d_f32_tiles.upload(pl->f32_tiles)) || (rc = pl->d_f32_out_tiles.upload(pl->f32_out_tiles)) ||
         (rc = pl->d_f32_tiles_hi.upload(pl->f32_tiles_hi)) ||
         (rc = pl->d_f32_out_tiles_hi.upload(pl->f32_out_tiles_hi)) ||
-        (rc = pl->d_shadow_il.alloc(std::max<int64_t>(pl->size_shadow_il, 1))) ||
-        (rc = pl->d_l21_il.alloc(std::max<int64_t>(pl->size_l21_il, 1))) ||
+        (rc = pl->d_f32_tiles_lo.upload(pl->f32_tiles_lo)) ||
+        (rc = pl->d_f32_out_tiles_lo.upload(pl->f32_out_tiles_lo)) ||
+        (rc = pl->d_shadow_il.alloc(std::max<int64_t>(2 * pl->size_shadow_il, 2))) ||
+        (rc = pl->d_l21_il.alloc(std::max<int64_t>(2 * pl->size_l21_il, 2))) ||
         (rc = pl->d_chol_items.upload(pl->chol_items)) || (rc = pl->d_chol_sl32.upload(pl->chol_sl32)) ||
         (rc = pl->d_chol_sl64.upload(pl->chol_sl64)) || (rc = pl->d_chol_tiles.upload(pl->chol_tiles)) ||
         (rc = pl->d_shadow.alloc((pl->factor_items[5].empty() && pl->chol_items.empty())
@@ -618,8 +624,9 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
             pl->narrow_pref[SYMPIX_PREC_FP64] = 0;
             pl->narrow_pref[SYMPIX_PREC_FP32] = 3;
             pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
-        } else if (value == 2.0 || value == 3.0) {  // the chunked border solve and the split kernel: FP32 only
-            pl->narrow_pref[SYMPIX_PREC_FP64] = 1;
+        } else if (value == 2.0 || value == 3.0) {
+            // the chunked border solve (FP32 and FP64) and the split kernel (FP32)
+            pl->narrow_pref[SYMPIX_PREC_FP64] = 2;
             pl->narrow_pref[SYMPIX_PREC_FP32] = (int)value;
             pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
         } else {
@@ -710,7 +717,8 @@ extern "C" int sympix_autotune(sympix_plan_t pl, const double *bl, const double 
         best = 1e30f;
         int best_k = pl->narrow_pref[factor_precision];
         for (int kk : {0, 1, 2, 3}) {
-            if (kk >= 2 && factor_precision != SYMPIX_PREC_FP32) continue;
+            if ((kk == 2 && factor_precision == SYMPIX_PREC_FP32X2) || (kk == 3 && factor_precision != SYMPIX_PREC_FP32))
+                continue;
             pl->narrow_pref[factor_precision] = kk;
             float ms = 0.0f;
             auto run = [&] {
@@ -839,6 +847,14 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
         f += (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
+    } else if (factor_precision == SYMPIX_PREC_FP64 && pband && pl->narrow_pref[SYMPIX_PREC_FP64] == 2) {
+        // w <= 12 on the FP64 shadow: transpose in, band pass, transfer, carry,
+        // solve and corner sums of each width range, corners, write-back; then
+        // the lane groups of 12 < w <= 16
+        const int ni = (int)pl->l21_items.size(), nlo = pl->l21_items_w8;
+        if (pl->f32_slices_fused > 0 && !pl->f32_tiles_lo.empty())
+            f += 3 + (ni > 0 ? 2 + 3 * (nlo > 0 ? 1 : 0) + 3 * (ni > nlo ? 1 : 0) : 0);
+        f += l2 ? 1 : 0;
     } else if (narrow) {
         f += (l1 ? 1 : 0) + (l2 ? 1 : 0);  // lane groups for 8 < w <= 16, beside the G-lane kernel
     } else {
@@ -907,7 +923,7 @@ extern "C" int sympix_plan_device_bytes(sympix_plan_t pl, size_t *bytes, size_t 
                pl->d_ring_off.bytes() + pl->d_ring_stride.bytes() + pl->d_l21_items.bytes() +
                pl->d_l21_slices.bytes() + pl->d_l21_first.bytes() + pl->d_l21_nch.bytes() + pl->d_l21_T.bytes() +
                pl->d_l21_P.bytes() + pl->d_l21_S.bytes() + pl->d_l21_C.bytes() + pl->d_split_flags.bytes() +
-               pl->d_split_bandres.bytes();
+               pl->d_split_bandres.bytes() + pl->d_f32_tiles_lo.bytes() + pl->d_f32_out_tiles_lo.bytes();
     for (const auto &kv : pl->coupling) b += kv.second.d_desc.bytes();
     for (int i = 0; i < 5; ++i) b += pl->d_items_pband[i].bytes();
     for (int i = 0; i < 6; ++i) b += pl->d_factor_items[i].bytes();

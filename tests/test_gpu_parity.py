@@ -40,10 +40,12 @@ def _err(a, b):
 
 
 def _run(S, dev, wl, grid=None, ring0=0, ring1=None, precision="fp64", storage="pband", factor=False,
-         ninv_h=None, radii=None, factor_precision=None):
+         ninv_h=None, radii=None, factor_precision=None, narrow=None):
     import torch
     grid = grid or S.Grid(wl.lmax)
     plan = S.Plan(grid, wl.radii() if radii is None else radii, ring0, ring1)
+    if narrow is not None:
+        plan.set_narrow_factor(narrow)
     bl = torch.tensor(wl.beams(), dtype=torch.float64, device=dev)
     dl = torch.tensor(wl.priors(), dtype=torch.float64, device=dev)
     if ninv_h is None:
@@ -357,15 +359,19 @@ def test_masked_everywhere_gives_prior_only(S, dev):
         assert _err(M, ref) <= TOL["fp32"]
 
 
-def test_indefinite_block_reports_pivot(S, dev):
+@pytest.mark.parametrize("narrow", [0, 1, 2])
+def test_indefinite_block_reports_pivot(S, dev, narrow):
     """A negative inverse-noise value makes blocks indefinite: info names the
-    first bad pivot exactly as the oracle's Cholesky does."""
+    first bad pivot exactly as the oracle's Cholesky does, in the band part
+    and in the corner, for each FP64 narrow-band kernel (the G-lane kernel,
+    the band and border passes, and the one-lane shadow path with the border
+    rows solved by column chunks)."""
     wl = W.WORKLOADS["lmax64"]
     grid = S.Grid(64)
     colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
     ninv = wl.ninv(colat)
     ninv[0, : grid.npix // 3] *= -40.0
-    r = _run(S, dev, wl, grid=grid, ninv_h=ninv, precision="fp64", factor=True)
+    r = _run(S, dev, wl, grid=grid, ninv_h=ninv, precision="fp64", factor=True, narrow=narrow)
     og = O.grid(64)
     bad = 0
     for j in range(og["nrings"]):
@@ -374,6 +380,36 @@ def test_indefinite_block_reports_pivot(S, dev):
         assert r["info"][j] == info, j
         bad += info > 0
     assert bad > 0
+
+
+@pytest.mark.parametrize("fprec,narrow", [("fp64", 0), ("fp64", 1), ("fp64", 2), ("fp32", 2), ("fp32", 3)])
+def test_indefinite_corner_reports_pivot(S, dev, fprec, narrow):
+    """A single negative inverse-noise pixel near the end of a ring leaves
+    every leading minor of the band rows positive and breaks the block in its
+    last w rows (the corner, after the border rows) or in the last band rows:
+    info is the oracle's pivot index there, for each FP64 narrow-band kernel
+    and for the FP32 shadow paths (whose rescue refactors such blocks in
+    FP64)."""
+    wl = W.WORKLOADS["lmax64"]
+    grid = S.Grid(64)
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    ninv = wl.ninv(colat)
+    for j, back in ((40, 3), (20, 9), (55, 1)):
+        n = int(grid.nring[j])
+        ninv[0, int(grid.ring_offset[j]) + (n - back) * int(grid.ring_stride[j])] *= -3.0
+    r = _run(S, dev, wl, grid=grid, ninv_h=ninv, precision="fp64", factor=True, factor_precision=fprec,
+             narrow=narrow)
+    og = O.grid(64)
+    corner = band = 0
+    for j in range(og["nrings"]):
+        ref, _ = O.block(og, wl.beams()[0], wl.priors()[0], wl.radii()[0], ninv[0], j)
+        _, info = O.cholesky(ref)
+        assert r["info"][j] == info, (j, int(r["info"][j]), info)
+        _, n, w, fmt = r["plan"].block_layout("pband", 0, j)
+        if info > 0 and fmt == S.BLOCK_PBAND:
+            corner += info > n - w
+            band += info <= n - w
+    assert corner >= 2 and band >= 1, (corner, band)
 
 
 # -- full size, in the bench's configuration ----------------------------------------------
@@ -391,13 +427,14 @@ def _oracle_block_3000(j, ninv0):
     return _ORACLE_3000[j]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32x2", "fp64"])
-def test_full_size_lmax3000_sampled(S, dev, precision):
+@pytest.mark.parametrize("precision,narrow", [("fp32", None), ("fp32x2", None), ("fp64", 0), ("fp64", 2)])
+def test_full_size_lmax3000_sampled(S, dev, precision, narrow):
     """l_max = 3000, FWHM 5': every block factors; sampled blocks match the
     oracle and their factors reproduce them, from the pole to the equator
-    (ring 1500, 6075 pixels, the longest elimination chain)."""
+    (ring 1500, 6075 pixels, the longest elimination chain); FP64 with the
+    G-lane kernel and with the shadow path of chunked border rows."""
     wl = W.WORKLOADS["lmax3000"]
-    r = _run(S, dev, wl, precision=precision, factor=True)
+    r = _run(S, dev, wl, precision=precision, factor=True, narrow=narrow)
     assert np.all(r["info"] == 0)
     plan = r["plan"]
     for j in (0, 2, 37, 250, 1500):

@@ -75,6 +75,8 @@ def test_step_wide_bands_match_direct_calls(storage, fprec):
     ("lmax500", "pband", "fp32", "fp32", 2),
     ("lmax500", "pband", "fp32", "fp32", 3),
     ("lmax500", "pband", "fp64", "fp64", -1),
+    ("lmax500", "pband", "fp64", "fp64", 2),
+    ("lmax64", "pband", "fp64", "fp64", 2),
     ("lmax64", "dense", "fp32x2", "fp32x2", -1),
 ])
 def test_step_matches_direct_calls(name, storage, sprec, fprec, narrow):
@@ -166,6 +168,11 @@ def test_trace_names_every_kernel():
     S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp32"), precision="fp32")
     names = [n for n, _ in plan.trace_read()]
     for k in ("k_f32_shadow_in", "k_f32_split", "k_f32_out"):
+        assert k in names, names
+    # FP64: the one-lane band pass on the FP64 shadow, then the chunked border rows
+    S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp64"), precision="fp64")
+    names = [n for n, _ in plan.trace_read()]
+    for k in ("k_f32_shadow_in", "k_f64_band_pass", "k_l21_transfer", "k_l21_corner", "k_f32_out"):
         assert k in names, names
     plan.set_narrow_factor(-1)
     assert plan.trace_read() == []
