@@ -55,8 +55,9 @@ def parse(argv=None):
                     help="replay the step as captured CUDA graphs, or call the entry points directly")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--narrow-factor", type=int, default=None, choices=[-1, 0, 1, 2, 3],
-                    help="kernel for bands w <= 12: 0 G-lane, 1 earlier kernels, 2 FP32 chunked border, "
-                         "3 FP32 split CTAs, -1 per arithmetic (default: the autotuner's choice)")
+                    help="kernel for bands w <= 12: 0 G-lane, 1 earlier kernels, 2 band pass and chunked "
+                         "border on a shadow of the arithmetic, 3 FP32 split CTAs, -1 per arithmetic (default: "
+                         "the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the l_max 1500 and 32-operator sub-lines")
@@ -307,6 +308,20 @@ def kernel_models(plan, grid, sprec, fprec):
     # chunk kernels are not modelled separately
     for name in ("k_l21_transfer", "k_l21_carry", "k_l21_solve", "k_l21_cornerpart", "k_l21_corner"):
         m[name] = (0.0, None, "fp32", "a phase of the chunked border solve, not modelled alone")
+    if fprec in ("fp64", "fp32x2"):
+        # FP64 / split FP32 on a shadow of 8-byte elements (option 2, w <= 12):
+        # the transposes move 16 B per element (FP64 read or written, the
+        # shadow element written or read), the band pass reads and writes its
+        # rows (16 B) and does the band third of the factor's flops
+        band_lo = sum(n * (w + 1) for n, w in narrow if w <= 12)
+        l21_lo = sum(w * (n - w) for n, w in narrow if w <= 12)
+        fl_band = sum((n - w) * w * (w + 1) + 2.0 * n for n, w in narrow if w <= 12)
+        m.update({"k_f32_shadow_in": (band_lo * 16.0, 0.0, fprec), "k_f32_out": ((band_lo + l21_lo) * 16.0, 0.0, fprec),
+                  "k_f64_band_pass": (band_lo * 16.0, fl_band, "fp64"),
+                  "k_df_band_pass": (band_lo * 16.0, fl_band, "fp32x2")})
+        for name in ("k_l21_transfer", "k_l21_carry", "k_l21_solve", "k_l21_cornerpart", "k_l21_corner"):
+            m[name] = (0.0, None, fprec, "a phase of the chunked border solve, not modelled alone")
+        return m
     m.update({"k_f32_shadow_in": (band * 12.0, 0.0, "fp32"), "k_f32_out": (band * 4.0 + l21 * 12.0, 0.0, "fp32"),
               "k_f32_fused": (b12, fl12, "fp32"), "k_f32_band_pass": (16.0 * band - b12, (fl - fl12) / 3, "fp32"),
               "k_f32_border_pass": (0.0, 2 * (fl - fl12) / 3, "fp32"),

@@ -152,16 +152,16 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           blocks, G lanes per block sharing the band window; 1 the
                                           earlier kernels (FP32: one lane per block on an FP32
                                           band copy, a band warp and border warps per CTA; FP64 /
-                                          split FP32: lane groups); 2 FP32 and FP64: the band
+                                          split FP32: lane groups); 2 every arithmetic: the band
                                           pass alone (one lane per block on a band copy of the
                                           arithmetic), then the border rows solved in parallel
                                           over column chunks; 3 FP32: for w <= 8 band and border
                                           passes in two CTAs of one cooperative launch (the
                                           kernel of 1 where they cannot all be resident),
-                                          9 <= w <= 12 as 2 beside it (3: FP64 as 2; 2, 3: split
-                                          FP32 as 1); -1 (default) per
+                                          9 <= w <= 12 as 2 beside it (3: FP64 and split FP32
+                                          as 2); -1 (default) per
                                           arithmetic, as measured at l_max 3000: FP64 0, FP32 3,
-                                          split FP32 1.  sympix_autotune times the candidates for
+                                          split FP32 2.  sympix_autotune times the candidates for
                                           its factor arithmetic */
 #define SYMPIX_OPT_WAIT_LIMIT 5       /* polls of a bounded device wait (default 2^22, about
                                           0.3 s): the FP32 factor's border warps wait for rows

@@ -56,6 +56,36 @@ __device__ __forceinline__ F2 f2_rsqrt(F2 x) {
     return f2_fast_two_sum(y, corr);
 }
 
+// A split-FP32 value as an arithmetic type, for the kernels templated on
+// their element type (the one-lane band pass and the chunked border rows):
+// the operations above behind operators.
+struct __align__(8) DF {  // one 8-byte access per value
+    float hi, lo;
+    DF() = default;
+    __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr explicit DF(float h) : hi(h), lo(0.0f) {}
+};
+__device__ __forceinline__ F2 to_f2(DF a) { return {a.hi, a.lo}; }
+__device__ __forceinline__ DF to_df(F2 a) { return {a.hi, a.lo}; }
+__device__ __forceinline__ DF operator-(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF operator+(DF a, DF b) { return to_df(f2_add(to_f2(a), to_f2(b))); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return to_df(f2_add(to_f2(a), f2_neg(to_f2(b)))); }
+__device__ __forceinline__ DF operator*(DF a, DF b) { return to_df(f2_mul(to_f2(a), to_f2(b))); }
+__device__ __forceinline__ DF &operator+=(DF &a, DF b) { return a = a + b; }
+__device__ __forceinline__ bool operator>(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+// a b + c: the exact product of the high parts (TwoProduct) and the cross
+// terms, added to c by a two-sum, then one renormalisation
+__device__ __forceinline__ DF df_fma(DF a, DF b, DF c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi, bb = s - p;
+    float t = (p - (s - bb)) + (c.hi - bb);
+    t += e + c.lo;
+    return to_df(f2_fast_two_sum(s, t));
+}
+
 // -- FP32 <-> FP64 on the integer ALU --------------------------------------
 // Type conversions to and from 64-bit floating point issue on the FP64 pipe,
 // which runs at 1/64 of the FP32 rate on GB300.  These helpers move the

@@ -52,13 +52,15 @@ extern "C" int sympix_factor_blocks(sympix_plan_t pl, int storage, int precision
     const bool dense = storage == SYMPIX_STORE_DENSE;
     trace_mark(pl, st, nullptr);
     // periodic-band storage: bands up to w = 12 go to the narrow-band kernel
-    // or (FP64 and FP32) to the one-lane-per-block shadow path, as the plan
+    // or (every arithmetic) to the one-lane-per-block shadow path, as the plan
     // selects, 12 < w <= 16 to the lane kernels; dense storage keeps the lane
     // kernels for every w <= 16
     const bool narrow = !dense && pl->narrow_pref[precision] == 0;
     if (narrow) launch_pband_chol(pl, precision, blocks, info, st);
     if (precision == SYMPIX_PREC_FP64 && !dense && pl->narrow_pref[precision] == 2) {
         launch_f64_slices(pl, blocks, info, st);  // w <= 12 on the FP64 shadow, lane groups above
+    } else if (precision == SYMPIX_PREC_FP32X2 && !dense && pl->narrow_pref[precision] == 2) {
+        launch_df_slices(pl, blocks, info, st);  // w <= 12 on a split-FP32 shadow, lane groups above
     } else if (precision == SYMPIX_PREC_FP64) {
         if (!narrow) launch_band<ArF64>(pl, dense, blocks, info, st);  // (narrow: every w <= 16 done)
         trace_mark(pl, st, "k_factor_band");

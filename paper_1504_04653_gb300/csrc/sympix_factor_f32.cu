@@ -77,15 +77,17 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict
     if (bi >= 0) info[bi] = r;
 }
 
-// FP64 band pass on the FP64 shadow, widths up to 12: one warp per slice,
-// one lane per block; info = i + 1 for the first row whose pivot is not
-// positive (the border kernels then leave the block alone).
-__global__ void __launch_bounds__(32) k_f64_band_pass(const F32Slice *__restrict__ slices,
-                                                      const int32_t *__restrict__ items,
-                                                      const BlockDesc *__restrict__ blocks, double *__restrict__ sh,
-                                                      int32_t *__restrict__ info) {
-    extern __shared__ __align__(16) unsigned char f64_smem[];
-    double *stage = reinterpret_cast<double *>(f64_smem);
+// Band pass on an FP64 (V = double) or split-FP32 (V = DF) shadow, widths
+// up to 12: one warp per slice, one lane per block; info = i + 1 for the
+// first row whose pivot is not positive (the border kernels then leave the
+// block alone).
+template <class V>
+__global__ void __launch_bounds__(32) k_exact_band_pass(const F32Slice *__restrict__ slices,
+                                                        const int32_t *__restrict__ items,
+                                                        const BlockDesc *__restrict__ blocks, V *__restrict__ sh,
+                                                        int32_t *__restrict__ info) {
+    extern __shared__ __align__(16) unsigned char exact_smem[];
+    V *stage = reinterpret_cast<V *>(exact_smem);
     const F32Slice sl = slices[blockIdx.x];
     const int lane = threadIdx.x;
     int m = 0, bi = -1;
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(32) k_f64_band_pass(const F32Slice *__restrict
         bi = items[sl.first + lane];
         m = blocks[bi].n - sl.w;
     }
-    const int r = F32BandDispatch<12, double>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, stage, 0.0f);
+    const int r = ExactBandDispatch<12, V>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, stage);
     if (bi >= 0) info[bi] = r;
 }
 
@@ -245,31 +247,46 @@ void launch_f32_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStre
     trace_mark(pl, st, "k_factor_rescue");
 }
 
-// The FP64 factor of the periodic bands up to w = 16 on an FP64 shadow:
-// for w <= 12 the transposes around the one-lane-per-block band pass and the
-// chunked border solve (every FP64 instruction does 32 blocks' work), for
-// 12 < w <= 16 the lane-group kernel.  The shadow and the chunk scratch are
-// the FP32 path's buffers, which the plan sizes for doubles.
-void launch_f64_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+// The FP64 (V = double) or split-FP32 (V = DF) factor of the periodic bands
+// up to w = 16 on a shadow of that element: for w <= 12 the transposes
+// around the one-lane-per-block band pass and the chunked border solve (every
+// instruction does 32 blocks' work), for 12 < w <= 16 the lane-group kernel.
+// The shadow and the chunk scratch are the FP32 path's buffers, which the
+// plan sizes for 8-byte elements.
+template <class V>
+static void launch_exact_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
     const int nf = pl->f32_slices_fused;
     const size_t nin = pl->f32_tiles_lo.size(), nout = pl->f32_out_tiles_lo.size();
     if (nf > 0 && nin > 0) {
         const F32Slice *sl = pl->d_f32_slices.p;
-        double *sh = reinterpret_cast<double *>(pl->d_shadow_il.p), *l21 = reinterpret_cast<double *>(pl->d_l21_il.p);
-        k_f32_shadow_in<double><<<(unsigned)nin, 256, 0, st>>>(pl->d_f32_tiles_lo.p, sl, pl->d_f32_items.p,
-                                                               pl->d_blocks.p, blocks, sh);
+        V *sh = reinterpret_cast<V *>(pl->d_shadow_il.p), *l21 = reinterpret_cast<V *>(pl->d_l21_il.p);
+        k_f32_shadow_in<V><<<(unsigned)nin, 256, 0, st>>>(pl->d_f32_tiles_lo.p, sl, pl->d_f32_items.p, pl->d_blocks.p,
+                                                          blocks, sh);
         trace_mark(pl, st, "k_f32_shadow_in");
-        const size_t smem = (size_t)2 * 13 * 13 * 32 * sizeof(double);
-        cudaFuncSetAttribute(k_f64_band_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_f64_band_pass<<<(unsigned)nf, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, sh, info);
-        trace_mark(pl, st, "k_f64_band_pass");
-        launch_f64_l21(pl, blocks, info, st);
-        k_f32_out<double><<<(unsigned)nout, 256, 0, st>>>(pl->d_f32_out_tiles_lo.p, sl, pl->d_f32_items.p,
-                                                          pl->d_blocks.p, info, sh, l21, blocks);
+        const size_t smem = (size_t)2 * 13 * 13 * 32 * sizeof(V);
+        cudaFuncSetAttribute(k_exact_band_pass<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_exact_band_pass<V><<<(unsigned)nf, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, sh, info);
+        trace_mark(pl, st, std::is_same<V, double>::value ? "k_f64_band_pass" : "k_df_band_pass");
+        if constexpr (std::is_same<V, double>::value)
+            launch_f64_l21(pl, blocks, info, st);
+        else
+            launch_df_l21(pl, blocks, info, st);
+        k_f32_out<V><<<(unsigned)nout, 256, 0, st>>>(pl->d_f32_out_tiles_lo.p, sl, pl->d_f32_items.p, pl->d_blocks.p,
+                                                     info, sh, l21, blocks);
         trace_mark(pl, st, "k_f32_out");
     }
-    launch_band<ArF64>(pl, false, blocks, info, st, 0, true);  // 12 < w <= 16
+    if constexpr (std::is_same<V, double>::value)
+        launch_band<ArF64>(pl, false, blocks, info, st, 0, true);  // 12 < w <= 16
+    else
+        launch_band<ArF2>(pl, false, blocks, info, st, 0, true);
     trace_mark(pl, st, "k_factor_band");
+}
+
+void launch_f64_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    launch_exact_slices<double>(pl, blocks, info, st);
+}
+void launch_df_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    launch_exact_slices<DF>(pl, blocks, info, st);
 }
 
 }  // namespace sympix

@@ -161,9 +161,10 @@ struct StaticFor<E, E> {
 // so that all take part in the staging); stage: the CTA's two period
 // buffers, laid out like the shadow.
 // T = float: FP32, pivots checked against the floor (a block below it
-// returns kRescue and is refactored in FP64).  T = double: FP64 on an FP64
-// shadow, the return value is LAPACK's info (i + 1 for the first row i whose
-// pivot is not positive; the lane stops there).
+// returns kRescue and is refactored in FP64).  T = double (FP64) or DF
+// (split FP32), on a shadow of that element: the return value is LAPACK's
+// info (i + 1 for the first row i whose pivot is not positive; the lane
+// stops there).
 // An element of the FP64 input in a shadow's arithmetic (FP32 on the integer
 // ALU, see sympix_arith.cuh), and back to FP64.
 template <class V>
@@ -172,9 +173,14 @@ template <>
 __device__ __forceinline__ float elem_from_f64<float>(double x) { return f64_to_f32_bits(x); }
 template <>
 __device__ __forceinline__ double elem_from_f64<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ DF elem_from_f64<DF>(double x) { return to_df(f2_from_bits(x)); }
 __device__ __forceinline__ double elem_to_f64(float x) { return f32_to_f64_bits(x); }
 __device__ __forceinline__ double elem_to_f64(double x) { return x; }
-// A 16-byte group of consecutive elements (four floats or two doubles).
+// split FP32: hi + lo is exact in FP64 (one FP64 add)
+__device__ __forceinline__ double elem_to_f64(DF x) { return f32_to_f64_bits(x.hi) + f32_to_f64_bits(x.lo); }
+// A 16-byte group of consecutive elements (four floats, two doubles or two
+// split-FP32 values).
 __device__ __forceinline__ void store16(float *p, const float *v) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -193,17 +199,34 @@ __device__ __forceinline__ void load16(const double *p, double *v) {
     v[0] = e.x;
     v[1] = e.y;
 }
+__device__ __forceinline__ void store16(DF *p, const DF *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+}
+__device__ __forceinline__ void load16(const DF *p, DF *v) {
+    const float4 e = *reinterpret_cast<const float4 *>(p);
+    v[0] = DF(e.x, e.y);
+    v[1] = DF(e.z, e.w);
+}
+// a read-only load through the non-coherent cache
+__device__ __forceinline__ float ldg_elem(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ldg_elem(const double *p) { return __ldg(p); }
+__device__ __forceinline__ DF ldg_elem(const DF *p) {
+    const float2 e = __ldg(reinterpret_cast<const float2 *>(p));
+    return DF(e.x, e.y);
+}
 
 __device__ __forceinline__ float band_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double band_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float band_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double band_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ DF band_rsqrt(DF x) { return to_df(f2_rsqrt(to_f2(x))); }
+__device__ __forceinline__ DF band_fma(DF a, DF b, DF c) { return df_fma(a, b, c); }
 
 template <class T, int W>
 __device__ __forceinline__ int band_lanes(T *shs, int lane, int m, int mmax, T *stage, float floor,
                                           volatile int *prog) {
     constexpr int RL = W + 1, CH = RL * RL;
-    constexpr bool F64 = sizeof(T) == 8;
+    constexpr bool EXACT = !std::is_same<T, float>::value;  // FP64 or split FP32: LAPACK's info
     constexpr int PER16 = 16 / (int)sizeof(T);  // elements per 16-byte copy
     T *band = shs + lane;  // element e at band[32 e]
     auto issue = [&](int per) {
@@ -230,8 +253,8 @@ __device__ __forceinline__ int band_lanes(T *shs, int lane, int m, int mmax, T *
     // The pivot d of row k and rs = 1/sqrt(d) arrive from the previous
     // step: each step forms the next pivot first (one product) and starts
     // its rsqrt before the rest of the update.
-    // FP32: the floor test; FP64: the first non-positive pivot (row + 1)
-    auto fails = [&](T dv, T odv) { return F64 ? !(dv > T(0)) : !(dv > T(floor) * odv); };
+    // FP32: the floor test; FP64 and split FP32: the first non-positive pivot (row + 1)
+    auto fails = [&](T dv, T odv) { return EXACT ? !(dv > T(0)) : !(dv > T(floor) * odv); };
     bool bad = m > 0 && fails(Wn[0][0], od[0]);
     int info = bad ? 1 : 0;
     T d = Wn[0][0], rs = band_rsqrt(Wn[0][0]);
@@ -305,10 +328,93 @@ __device__ __forceinline__ int band_lanes(T *shs, int lane, int m, int mmax, T *
         __syncwarp();
         if (lane == 0) *prog = 0x7fffffff;
     }
-    if constexpr (F64)
+    if constexpr (EXACT)
         return info;
     else
         return bad ? kRescue : 0;
+}
+
+// The same band pass for FP64 (T = double) and split FP32 (T = DF), whose
+// steps are several times longer: a period unrolled as above would not fit
+// the instruction cache, so the steps run as a loop over one body, and the
+// window moves through the registers instead (Wn[r][c] holds rows k+r,
+// columns k+c; after the update every entry shifts up and left by one,
+// W (W+1)/2 moves, and row k+1+W enters at the bottom).  Same staging, same
+// order of operations per entry, same return value (LAPACK's info).
+template <class T, int W>
+__device__ __forceinline__ int band_lanes_loop(T *shs, int lane, int m, int mmax, T *stage) {
+    constexpr int RL = W + 1, CH = RL * RL;
+    constexpr int PER16 = 16 / (int)sizeof(T);
+    T *band = shs + lane;
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < mmax) {
+            T *dst = stage + (per & 1) * CH * 32;
+            const T *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = lane; i < CH * 32 / PER16; i += 32) cp_async16(dst + PER16 * i, src + PER16 * i);
+        }
+        cp_async_commit();
+    };
+    issue(1);
+    T Wn[RL][RL];
+#pragma unroll
+    for (int r = 0; r <= W; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) Wn[r][c] = r < m ? band[((int64_t)r * RL + (r - c)) * 32] : T(0);
+    bool bad = m > 0 && !(Wn[0][0] > T(0));
+    int info = bad ? 1 : 0;
+    T d = Wn[0][0], rs = band_rsqrt(Wn[0][0]);
+    const int PW = mmax / RL;
+    for (int p = 0; p <= PW; ++p) {
+        issue(p + 2);
+        cp_async_wait<1>();
+        __syncwarp();
+        const T *src = stage + ((p + 1) & 1) * CH * 32 + lane;
+        T *lrow = band + (int64_t)p * RL * RL * 32;
+        const int kend = min(RL, m - p * RL);  // this lane's steps in the period
+#pragma unroll 1
+        for (int ph = 0; ph < kend; ++ph) {
+            lrow[ph * RL * 32] = d * rs;
+            T l[RL];
+            T dn = T(0), rsn = T(0);
+            if constexpr (W >= 1) {
+                l[1] = Wn[1][0] * rs;
+                dn = band_fma(-l[1], l[1], Wn[1][1]);
+                rsn = band_rsqrt(dn);
+            }
+#pragma unroll
+            for (int r = 2; r <= W; ++r) l[r] = Wn[r][0] * rs;
+#pragma unroll
+            for (int r = 1; r <= W; ++r) lrow[((ph + r) * RL + r) * 32] = l[r];
+#pragma unroll
+            for (int r = 1; r <= W; ++r)
+#pragma unroll
+                for (int c = 1; c <= r; ++c)
+                    if (r > 1 || c > 1) Wn[r][c] = band_fma(-l[r], l[c], Wn[r][c]);
+            // shift by one row and column; row k+1+W enters at the bottom
+#pragma unroll
+            for (int r = 0; r < W; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c) Wn[r][c] = Wn[r + 1][c + 1];
+#pragma unroll
+            for (int c = 0; c <= W; ++c) Wn[W][c] = src[(ph * RL + (W - c)) * 32];
+            if constexpr (W >= 1) {
+                d = dn;
+                rs = rsn;
+            } else {
+                d = Wn[0][0];
+                rs = band_rsqrt(d);
+            }
+            const int k = p * RL + ph;
+            const bool f = k + 1 < m && !(d > T(0));
+            if (f && !bad) info = k + 2;
+            bad |= f;
+        }
+        if (bad) m = 0;
+        __syncwarp();
+    }
+    cp_async_wait<0>();
+    return info;
 }
 
 template <int W>
@@ -330,6 +436,20 @@ struct F32BandDispatch<0, T> {
     __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage, float floor,
                               volatile int *prog = nullptr) {
         return w == 0 ? band_lanes<T, 0>(shs, lane, m, mmax, stage, floor, prog) : -1;
+    }
+};
+
+template <int W, class T>
+struct ExactBandDispatch {
+    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage) {
+        if (w == W) return band_lanes_loop<T, W>(shs, lane, m, mmax, stage);
+        return ExactBandDispatch<W - 1, T>::run(w, shs, lane, m, mmax, stage);
+    }
+};
+template <class T>
+struct ExactBandDispatch<0, T> {
+    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage) {
+        return w == 0 ? band_lanes_loop<T, 0>(shs, lane, m, mmax, stage) : -1;
     }
 };
 
@@ -778,8 +898,11 @@ void launch_f32_split_w8(sympix_plan_t pl, double *blocks, int32_t *info, cudaSt
 void launch_f32_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st, bool hi_only = false);
 // the same in FP64 on the FP64 band shadow (every fused-range slice)
 void launch_f64_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
-// the FP64 factor of the periodic bands up to w = 16 (sympix_factor_f32.cu)
+void launch_df_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+// the FP64 / split-FP32 factor of the periodic bands up to w = 16 on a
+// shadow of that arithmetic (sympix_factor_f32.cu)
 void launch_f64_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
+void launch_df_slices(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st);
 constexpr int kDefaultWaitLimit = 1 << 22;  // polls of a bounded device wait (about 0.3 s)
 void launch_factor_wide_dense(sympix_plan_t pl, int precision, bool dense, double *blocks, int32_t *info,
                               cudaStream_t st);

@@ -290,10 +290,12 @@ struct sympix_plan_s {
     // kernel for periodic bands w <= 12, per factor arithmetic (SYMPIX_PREC_*):
     // 0 k_pband_chol (G lanes per block), 1 the earlier kernels (FP32: the
     // two-role kernel on an FP32 band copy; FP64 / split FP32: lane groups),
-    // 2 (FP32) band pass and chunked border solve, 3 (FP32) band and border
-    // CTAs of one cooperative launch for w <= 8, 2 for 9 <= w <= 12.
-    // Defaults from measurement at l_max = 3000: FP64 0, FP32 3, split FP32 1.
-    int narrow_pref[3] = {0, 3, 1};
+    // 2 band pass and chunked border solve on a shadow of the arithmetic,
+    // 3 (FP32) band and border CTAs of one cooperative launch for w <= 8, 2
+    // for 9 <= w <= 12.  Defaults from measurement at l_max = 3000 (factor
+    // stage): FP64 0 (20.1 ms; 2: 23.4 ms), FP32 3, split FP32 2 (7.9 ms;
+    // 1: 30.2 ms).
+    int narrow_pref[3] = {0, 3, 2};
     int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;

@@ -34,7 +34,7 @@ struct L21Carry {
                 for (int j = 0; j < W; ++j) {
                     const V sj = sb[j];
 #pragma unroll
-                    for (int i = 0; i < W; ++i) r[i] = band_fma(sj, __ldg(t + j * W + i), r[i]);
+                    for (int i = 0; i < W; ++i) r[i] = band_fma(sj, ldg_elem(t + j * W + i), r[i]);
                 }
 #pragma unroll
                 for (int i = 0; i < W; ++i) sn[b * W + i] = r[i];
@@ -224,6 +224,14 @@ void launch_f64_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_
     launch_l21<double>(pl, c, reinterpret_cast<double *>(pl->d_l21_T.p), reinterpret_cast<double *>(pl->d_l21_P.p),
                        reinterpret_cast<double *>(pl->d_l21_S.p), reinterpret_cast<double *>(pl->d_l21_C.p), info, st,
                        false);
+}
+
+// Split FP32: the same buffers, read as (hi, lo) float pairs.
+void launch_df_l21(sympix_plan_t pl, double *blocks, int32_t *info, cudaStream_t st) {
+    const L21Ctx<DF> c{pl->d_f32_slices.p, pl->d_f32_items.p, info, pl->d_blocks.p,
+                       reinterpret_cast<DF *>(pl->d_shadow_il.p), reinterpret_cast<DF *>(pl->d_l21_il.p), blocks};
+    launch_l21<DF>(pl, c, reinterpret_cast<DF *>(pl->d_l21_T.p), reinterpret_cast<DF *>(pl->d_l21_P.p),
+                   reinterpret_cast<DF *>(pl->d_l21_S.p), reinterpret_cast<DF *>(pl->d_l21_C.p), info, st, false);
 }
 
 int l21_chunk_cols_host(int w) { return l21_chunk_cols(w); }

@@ -1,5 +1,6 @@
 // Border rows of the periodic-band factor, L21 = A21 L11^-T, in parallel
-// over column chunks, in FP32 (V = float) or FP64 (V = double).
+// over column chunks, in FP32 (V = float), FP64 (V = double) or split FP32
+// (V = DF).
 //
 // With L11 known (the band pass has run), each border row obeys the linear
 // recurrence
@@ -63,10 +64,7 @@ __device__ __forceinline__ void l21_store_mat(V *mat, int lane, const V (&v)[W][
             const int x = P16 * q + t;
             e[t] = x < W * W ? v[x / W][x % W] : V(0);
         }
-        if constexpr (P16 == 4)
-            reinterpret_cast<float4 *>(d)[q] = make_float4(e[0], e[1], e[2], e[3]);
-        else
-            reinterpret_cast<double2 *>(d)[q] = make_double2(e[0], e[1]);
+        store16(d + P16 * q, e);
     }
 }
 template <class V, int W>
@@ -76,17 +74,7 @@ __device__ __forceinline__ void l21_load_mat(const V *mat, int lane, V (&v)[W * 
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         V t[P16];
-        if constexpr (P16 == 4) {
-            const float4 e = reinterpret_cast<const float4 *>(s)[q];
-            t[0] = e.x;
-            t[1] = e.y;
-            t[2] = e.z;
-            t[3] = e.w;
-        } else {
-            const double2 e = reinterpret_cast<const double2 *>(s)[q];
-            t[0] = e.x;
-            t[1] = e.y;
-        }
+        load16(s + P16 * q, t);
 #pragma unroll
         for (int u = 0; u < P16; ++u)
             if (P16 * q + u < W * W) v[P16 * q + u] = t[u];
@@ -224,14 +212,14 @@ __device__ __forceinline__ void l21_run(V (&y)[NR][W], int b0, const V *__restri
 // Rows per warp and warps per item of a width.  FP32: up to 8 one warp
 // holds all rows (and forms the pair sums); wider bands spread 3 rows over
 // each of 4 warps, which shortens the per-item chain those few blocks would
-// set.  FP64 (twice the registers per value, and its pipe the limit): up to
-// 8 rows over 2 warps, 9 to 12 over 4.  The warp count is the same for
+// set.  FP64 and split FP32 (twice the registers per value): up to 8 rows
+// over 2 warps, 9 to 12 over 4.  The warp count is the same for
 // every width of one launch range (1..8, 9..12): it is the CTA's, and all
 // its warps take part in the staging and its barriers.
 template <class V, int W>
 struct L21Split {
-    static constexpr bool F64 = sizeof(V) == 8;
-    static constexpr int NWARP = W <= 8 ? (F64 ? 2 : 1) : 4;
+    static constexpr bool WIDE = sizeof(V) == 8;  // two registers a value
+    static constexpr int NWARP = W <= 8 ? (WIDE ? 2 : 1) : 4;
     static constexpr int NR = (W + NWARP - 1) / NWARP;
 };
 

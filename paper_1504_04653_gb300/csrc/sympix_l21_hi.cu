@@ -1,5 +1,5 @@
-// Chunked border solve, widths 9..12: the transfer and solve kernels in FP32
-// and FP64 (one translation unit per width range, compiled in parallel).
+// Chunked border solve, widths 9..12: the transfer and solve kernels in FP32,
+// FP64 and split FP32 (one translation unit per width range, compiled in parallel).
 #include "sympix_l21.cuh"
 
 namespace sympix {
@@ -30,5 +30,9 @@ template void launch_l21_solve_hi<float>(const L21Ctx<float> &, const int2 *, co
                                          cudaStream_t);
 template void launch_l21_solve_hi<double>(const L21Ctx<double> &, const int2 *, const double *, double *, int, int,
                                           cudaStream_t);
+
+template void launch_l21_transfer_hi<DF>(const L21Ctx<DF> &, const int2 *, const int32_t *, DF *, DF *, DF *, DF *, int,
+                                      int, cudaStream_t);
+template void launch_l21_solve_hi<DF>(const L21Ctx<DF> &, const int2 *, const DF *, DF *, int, int, cudaStream_t);
 
 }  // namespace sympix

@@ -623,12 +623,12 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         if (value == -1.0) {
             pl->narrow_pref[SYMPIX_PREC_FP64] = 0;
             pl->narrow_pref[SYMPIX_PREC_FP32] = 3;
-            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
+            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 2;
         } else if (value == 2.0 || value == 3.0) {
-            // the chunked border solve (FP32 and FP64) and the split kernel (FP32)
+            // the chunked border solve (every arithmetic) and the split kernel (FP32)
             pl->narrow_pref[SYMPIX_PREC_FP64] = 2;
             pl->narrow_pref[SYMPIX_PREC_FP32] = (int)value;
-            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 1;
+            pl->narrow_pref[SYMPIX_PREC_FP32X2] = 2;
         } else {
             for (int &v : pl->narrow_pref) v = (int)value;
         }
@@ -717,8 +717,7 @@ extern "C" int sympix_autotune(sympix_plan_t pl, const double *bl, const double 
         best = 1e30f;
         int best_k = pl->narrow_pref[factor_precision];
         for (int kk : {0, 1, 2, 3}) {
-            if ((kk == 2 && factor_precision == SYMPIX_PREC_FP32X2) || (kk == 3 && factor_precision != SYMPIX_PREC_FP32))
-                continue;
+            if (kk == 3 && factor_precision != SYMPIX_PREC_FP32) continue;
             pl->narrow_pref[factor_precision] = kk;
             float ms = 0.0f;
             auto run = [&] {
@@ -847,8 +846,8 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
         }
     } else if (factor_precision == SYMPIX_PREC_FP32) {
         f += (l0 || l1 || l2) ? 2 : 0;  // both passes for every width up to 16
-    } else if (factor_precision == SYMPIX_PREC_FP64 && pband && pl->narrow_pref[SYMPIX_PREC_FP64] == 2) {
-        // w <= 12 on the FP64 shadow: transpose in, band pass, transfer, carry,
+    } else if (factor_precision != SYMPIX_PREC_FP32 && pband && pl->narrow_pref[factor_precision] == 2) {
+        // w <= 12 on the FP64 / split-FP32 shadow: transpose in, band pass, transfer, carry,
         // solve and corner sums of each width range, corners, write-back; then
         // the lane groups of 12 < w <= 16
         const int ni = (int)pl->l21_items.size(), nlo = pl->l21_items_w8;

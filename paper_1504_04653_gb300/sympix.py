@@ -231,9 +231,9 @@ class Plan:
         return self.tuning()
 
     def set_narrow_factor(self, kernel: int):
-        """w <= 12 bands: 0 the G-lane kernel, 1 the earlier kernels, 2 (FP32 and FP64) the band pass
-        and the border rows by column chunks, 3 (FP32; FP64 as 2) band and border passes in two CTAs of
-        one cooperative launch, -1 per arithmetic (default)."""
+        """w <= 12 bands: 0 the G-lane kernel, 1 the earlier kernels, 2 (every arithmetic) the band
+        pass and the border rows by column chunks, 3 (FP32; the others as 2) band and border passes in
+        two CTAs of one cooperative launch, -1 per arithmetic (default)."""
         _check(lib().sympix_plan_option(self._h, OPT_NARROW_FACTOR, float(kernel)))
 
     def set_wait_limit(self, polls: int):

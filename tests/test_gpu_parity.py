@@ -382,14 +382,15 @@ def test_indefinite_block_reports_pivot(S, dev, narrow):
     assert bad > 0
 
 
-@pytest.mark.parametrize("fprec,narrow", [("fp64", 0), ("fp64", 1), ("fp64", 2), ("fp32", 2), ("fp32", 3)])
+@pytest.mark.parametrize("fprec,narrow", [("fp64", 0), ("fp64", 1), ("fp64", 2), ("fp32", 2), ("fp32", 3),
+                                          ("fp32x2", 1), ("fp32x2", 2)])
 def test_indefinite_corner_reports_pivot(S, dev, fprec, narrow):
     """A single negative inverse-noise pixel near the end of a ring leaves
     every leading minor of the band rows positive and breaks the block in its
     last w rows (the corner, after the border rows) or in the last band rows:
-    info is the oracle's pivot index there, for each FP64 narrow-band kernel
-    and for the FP32 shadow paths (whose rescue refactors such blocks in
-    FP64)."""
+    info is the oracle's pivot index there, for each FP64 narrow-band kernel,
+    the split-FP32 kernels, and the FP32 shadow paths (whose rescue
+    refactors such blocks in FP64)."""
     wl = W.WORKLOADS["lmax64"]
     grid = S.Grid(64)
     colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
@@ -427,12 +428,14 @@ def _oracle_block_3000(j, ninv0):
     return _ORACLE_3000[j]
 
 
-@pytest.mark.parametrize("precision,narrow", [("fp32", None), ("fp32x2", None), ("fp64", 0), ("fp64", 2)])
+@pytest.mark.parametrize("precision,narrow", [("fp32", None), ("fp32x2", 1), ("fp32x2", 2), ("fp64", 0),
+                                              ("fp64", 2)])
 def test_full_size_lmax3000_sampled(S, dev, precision, narrow):
     """l_max = 3000, FWHM 5': every block factors; sampled blocks match the
     oracle and their factors reproduce them, from the pole to the equator
-    (ring 1500, 6075 pixels, the longest elimination chain); FP64 with the
-    G-lane kernel and with the shadow path of chunked border rows."""
+    (ring 1500, 6075 pixels, the longest elimination chain); FP64 and split
+    FP32 with their earlier kernels and with the shadow path of chunked
+    border rows."""
     wl = W.WORKLOADS["lmax3000"]
     r = _run(S, dev, wl, precision=precision, factor=True, narrow=narrow)
     assert np.all(r["info"] == 0)
@@ -784,7 +787,7 @@ def test_narrow_factor_matches_earlier_kernels(S, dev, fprec):
     plan.set_narrow_factor(1)
     ib = S.sympix_factor_blocks(plan, b, precision=fprec).cpu().numpy()
     plan.set_narrow_factor(-1)
-    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 3, "fp32x2": 1}
+    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 3, "fp32x2": 2}
     assert np.array_equal(ia, ib) and np.all(ia == 0)
     A, B = a.cpu().numpy(), b.cpu().numpy()
     tol = {"fp64": 1e-13, "fp32x2": 1e-11, "fp32": 1e-5}[fprec]

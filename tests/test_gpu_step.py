@@ -77,6 +77,7 @@ def test_step_wide_bands_match_direct_calls(storage, fprec):
     ("lmax500", "pband", "fp64", "fp64", -1),
     ("lmax500", "pband", "fp64", "fp64", 2),
     ("lmax64", "pband", "fp64", "fp64", 2),
+    ("lmax500", "pband", "fp32x2", "fp32x2", 2),
     ("lmax64", "dense", "fp32x2", "fp32x2", -1),
 ])
 def test_step_matches_direct_calls(name, storage, sprec, fprec, narrow):
@@ -173,6 +174,11 @@ def test_trace_names_every_kernel():
     S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp64"), precision="fp64")
     names = [n for n, _ in plan.trace_read()]
     for k in ("k_f32_shadow_in", "k_f64_band_pass", "k_l21_transfer", "k_l21_corner", "k_f32_out"):
+        assert k in names, names
+    # split FP32: the same on a split-FP32 shadow
+    S.sympix_factor_blocks(plan, S.sympix_sample_blocks(plan, ninv, precision="fp64"), precision="fp32x2")
+    names = [n for n, _ in plan.trace_read()]
+    for k in ("k_f32_shadow_in", "k_df_band_pass", "k_l21_transfer", "k_l21_corner", "k_f32_out"):
         assert k in names, names
     plan.set_narrow_factor(-1)
     assert plan.trace_read() == []
