@@ -72,6 +72,11 @@ def lib():
         L.sympix_oracle_block_pair.argtypes = [ctypes.c_int, _dptr, _i32ptr, _i64ptr, _i32ptr,
                                                ctypes.c_int, _dptr, _dptr, ctypes.c_double,
                                                _dptr, ctypes.c_int, ctypes.c_int, _dptr]
+        L.sympix_oracle_tiles_coupled.argtypes = [ctypes.c_int, ctypes.c_int, _i32ptr, ctypes.c_int, ctypes.c_long,
+                                                  ctypes.c_int, ctypes.c_long]
+        L.sympix_oracle_band_block.restype = ctypes.c_long
+        L.sympix_oracle_band_block.argtypes = [ctypes.c_int, _dptr, _i32ptr, _i64ptr, _i32ptr, ctypes.c_int,
+                                               ctypes.c_int, _dptr, _dptr, _dptr, ctypes.c_int, _dptr]
         L.sympix_oracle_trisolve.argtypes = [ctypes.c_int, _dptr, _dptr, ctypes.c_int, _dptr]
         L.sympix_oracle_support_margin.restype = ctypes.c_double
         L.sympix_oracle_support_margin.argtypes = [ctypes.c_int, _dptr, _i32ptr, ctypes.c_double,
@@ -251,6 +256,35 @@ def block_pair(g: dict, bl: np.ndarray, dl: np.ndarray, r_s: float, ninv: np.nda
     triples = lib().sympix_oracle_block_pair(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), _p(off, _i64ptr),
                                              _p(st, _i32ptr), g["lmax"], _p(b, _dptr), _p(d, _dptr), float(r_s),
                                              _p(nv, _dptr), int(j), int(k), _p(M, _dptr))
+    return M, int(triples)
+
+
+def tiles_coupled(g: dict, ra: int, ca: int, rb: int, cb: int) -> bool:
+    """Tile adjacency of two pixels of a DP grid (Sec. 2.3 tiling, Sec. 4.2)."""
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    return bool(lib().sympix_oracle_tiles_coupled(g["nrings"], g["k"], _p(nr, _i32ptr), int(ra), int(ca),
+                                                  int(rb), int(cb)))
+
+
+def band_block(g: dict, bl: np.ndarray, dl: np.ndarray, ninv: np.ndarray, band: int):
+    """Dense block of band `band` (k rings) of a DP grid under tile adjacency,
+    in the band's pixel order, and the triples summed."""
+    k = g["k"]
+    K = k * int(g["nring"][band * k])
+    M = np.zeros((K, K), dtype=np.float64)
+    th = _f64(g["theta"])
+    nr = np.ascontiguousarray(g["nring"], dtype=np.int32)
+    off = np.ascontiguousarray(g["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g["ring_stride"], dtype=np.int32)
+    b = _f64(bl)
+    d = _f64(dl)
+    nv = _f64(ninv)
+    assert len(nv) == g["npix"]
+    triples = lib().sympix_oracle_band_block(g["nrings"], _p(th, _dptr), _p(nr, _i32ptr), _p(off, _i64ptr),
+                                             _p(st, _i32ptr), k, g["lmax"], _p(b, _dptr), _p(d, _dptr),
+                                             _p(nv, _dptr), int(band), _p(M, _dptr))
+    if triples < 0:
+        raise ValueError("not a band of the grid")
     return M, int(triples)
 
 

@@ -625,3 +625,101 @@ long sympix_oracle_ordering(int N, int k, const int32_t *nring, int64_t *ring_of
     }
     return pos;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tile adjacency on a DP grid, and the block of one band (Sec. 2.3 tiling, */
+/* Sec. 4.2 locality approximation)                                         */
+/* ------------------------------------------------------------------------ */
+
+/* The paper partitions a grid of k-ring bands into k x k tiles (k columns of
+ * the band's k rings) and takes D^_ij = B^_ij = 0 unless pixels i and j lie
+ * in the same or in neighbouring tiles.  It does not say which tiles of two
+ * bands with different tile counts are neighbours.  Reading used here:
+ *   - bands are numbered by latitude, g = ring / k (north pole to south
+ *     pole); tiles of bands g and g' can be neighbours only if |g - g'| <= 1
+ *     (so the two bands next to the equator are neighbours);
+ *   - tile a of a band with T tiles spans the longitudes [a/T, (a+1)/T] of a
+ *     turn; two tiles are neighbours when these closed arcs meet (overlap or
+ *     touch) on the circle;
+ *   - inside a polar band (g = 0 or the last) every two tiles are
+ *     neighbours: the tiles meet across the pole.
+ * Returns 1 when pixel ca of ring ra and pixel cb of ring rb are coupled. */
+int sympix_oracle_tiles_coupled(int nrings, int k, const int32_t *nring, int ra, long ca, int rb, long cb)
+{
+    int ga = ra / k, gb = rb / k;
+    int G = nrings / k;
+    if (ga - gb > 1 || gb - ga > 1) return 0;
+    if (ga == gb && (ga == 0 || ga == G - 1)) return 1;
+    long Ta = nring[ra] / k, Tb = nring[rb] / k;
+    long a = ca / k, b = cb / k;
+    /* arcs [a/Ta, (a+1)/Ta] and [(b+s Tb)/Tb, (b+s Tb+1)/Tb] for a turn s */
+    for (long s = -1; s <= 1; ++s) {
+        long bb = b + s * Tb;
+        if (a * Tb <= (bb + 1) * Ta && bb * Ta <= (a + 1) * Tb) return 1;
+    }
+    return 0;
+}
+
+/* Dense block M (K x K, row-major, K = k n_g) of band g of a DP grid, in the
+ * band's own pixel order: row i is the pixel with grid index
+ * band_start + i, band_start the smallest grid index of the band's pixels.
+ *   M_qr = [q, r coupled] d(q.r)
+ *        + sum over pixels p of the grid coupled to both q and r of
+ *          b(p.q) N^-1_p b(p.r),
+ * "coupled" as sympix_oracle_tiles_coupled says (Eq. system-rewritten,
+ * Eq. Dhat with Y2 = Y1 under the tile truncation).  Summed p by p as
+ * sympix_oracle_block does.  Returns the triples summed, or -1 when g is not
+ * a band of the grid. */
+long sympix_oracle_band_block(int nrings, const double *theta, const int32_t *nring,
+                              const int64_t *ring_offset, const int32_t *ring_stride, int k,
+                              int lmax, const double *bl, const double *dl, const double *ninv,
+                              int g, double *M)
+{
+    if (k < 1 || nrings % k || g < 0 || g >= nrings / k) return -1;
+    int r0 = g * k;
+    long nb = nring[r0];
+    long K = (long)k * nb;
+    int64_t start = ring_offset[r0];
+    for (int r = r0; r < r0 + k; ++r)
+        if (ring_offset[r] < start) start = ring_offset[r];
+    memset(M, 0, sizeof(double) * (size_t)K * K);
+    /* row index of pixel c of ring r of the band */
+#define BAND_ROW(r, c) ((long)(ring_offset[(r)] + (c) * (int64_t)ring_stride[(r)] - start))
+
+    /* D^ inside the band */
+    for (int ra = r0; ra < r0 + k; ++ra)
+        for (long ca = 0; ca < nb; ++ca)
+            for (int rb = r0; rb < r0 + k; ++rb)
+                for (long cb = 0; cb < nb; ++cb) {
+                    if (!sympix_oracle_tiles_coupled(nrings, k, nring, ra, ca, rb, cb)) continue;
+                    double u = sympix_oracle_u(theta[ra], (int)nb, ca, theta[rb], (int)nb, cb);
+                    M[BAND_ROW(ra, ca) * K + BAND_ROW(rb, cb)] += sympix_oracle_kernel_u(lmax, dl, u);
+                }
+
+    /* B^T N^-1 B^ */
+    long triples = 0;
+    long *idx = (long *)malloc(sizeof(long) * K);
+    double *val = (double *)malloc(sizeof(double) * K);
+    for (int rho = 0; rho < nrings; ++rho) {
+        if (rho / k < g - 1 || rho / k > g + 1) continue; /* no tile of band g has a neighbour there */
+        for (long p = 0; p < nring[rho]; ++p) {
+            long cnt = 0;
+            for (int ra = r0; ra < r0 + k; ++ra)
+                for (long ca = 0; ca < nb; ++ca) {
+                    if (!sympix_oracle_tiles_coupled(nrings, k, nring, rho, p, ra, ca)) continue;
+                    double u = sympix_oracle_u(theta[ra], (int)nb, ca, theta[rho], nring[rho], p);
+                    idx[cnt] = BAND_ROW(ra, ca);
+                    val[cnt] = sympix_oracle_kernel_u(lmax, bl, u);
+                    ++cnt;
+                }
+            double np = ninv[ring_offset[rho] + p * (int64_t)ring_stride[rho]];
+            for (long x = 0; x < cnt; ++x)
+                for (long y = 0; y < cnt; ++y) M[(size_t)idx[x] * K + idx[y]] += val[x] * np * val[y];
+            triples += cnt * cnt;
+        }
+    }
+#undef BAND_ROW
+    free(idx);
+    free(val);
+    return triples;
+}

@@ -634,3 +634,89 @@ def test_trisolve_matches_scipy():
     L[1, 1] = 0.0
     with pytest.raises(ValueError):
         O.trisolve(L, np.ones(3))
+
+
+# -- tile adjacency and band blocks on DP grids (Sec. 2.3 tiling, Sec. 4.2) -----
+
+def _tile_mask(g):
+    """Tile adjacency of every pixel pair of a DP grid, by the circular
+    distance of the tiles' centre longitudes against the sum of their half
+    widths, in integers (units of 1 / (2 Ta Tb) of a turn); bands within one
+    of each other by latitude; every pair inside a polar band."""
+    _, _, ring, col = _pixel_angles(g)
+    k = g["k"]
+    G = g["nrings"] // k
+    band = ring // k
+    T = g["nring"][ring].astype(np.int64) // k
+    a = col.astype(np.int64) // k
+    Ta, Tb = T[:, None], T[None, :]
+    L = 2 * Ta * Tb
+    D = np.abs((2 * a[:, None] + 1) * Tb - (2 * a[None, :] + 1) * Ta) % L
+    meet = np.minimum(D, L - D) <= Ta + Tb
+    near = np.abs(band[:, None] - band[None, :]) <= 1
+    polar = (band[:, None] == band[None, :]) & ((band[:, None] == 0) | (band[:, None] == G - 1))
+    return near & (meet | polar)
+
+
+@pytest.mark.parametrize("lmax,k", [(23, 2), (47, 4), (63, 8)])
+def test_tile_adjacency_matches_arc_geometry(lmax, k):
+    """The oracle's tile rule against the centre-distance form of "two closed
+    arcs of a turn meet", for every tile pair of every band pair (one pixel
+    per tile, rings from the band's edges), and its shape: symmetric, three
+    tiles of its own band for a tile of a non-polar band, all tiles of a
+    polar band."""
+    g = O.grid(lmax, k=k, layout="dp", thr=0.0)
+    mask = _tile_mask(g)
+    G = g["nrings"] // k
+    for gi in range(G):
+        for gj in range(max(0, gi - 2), min(G, gi + 3)):
+            ra, rb = gi * k, gj * k + k - 1
+            Ta, Tb = g["nring"][ra] // k, g["nring"][rb] // k
+            for a in range(Ta):
+                for b in range(Tb):
+                    ca, cb = a * k + (a % k), b * k + k - 1
+                    pa = g["ring_offset"][ra] + ca * g["ring_stride"][ra]
+                    pb = g["ring_offset"][rb] + cb * g["ring_stride"][rb]
+                    want = bool(mask[pa, pb])
+                    assert O.tiles_coupled(g, ra, ca, rb, cb) == want, (gi, gj, a, b)
+                    assert O.tiles_coupled(g, rb, cb, ra, ca) == want
+            if gi == gj:
+                row = [O.tiles_coupled(g, ra, 0, rb, b * k) for b in range(Tb)]
+                if gi in (0, G - 1):
+                    assert all(row)
+                elif Ta >= 3:
+                    assert sum(row) == 3 and row[0] and row[1] and row[-1]
+
+
+@pytest.mark.parametrize("lmax,k", [(15, 2), (31, 4), (23, 8)])
+def test_band_block_matches_dense_brute_force(lmax, k):
+    """Every band block of a DP grid equals the band's diagonal block of the
+    dense D^ + B^T diag(N^-1) B^ under tile adjacency, built here from
+    3-vector dot products, numpy's Legendre series and the centre-distance
+    tile mask, with N^-1 holding masked zeros."""
+    from numpy.polynomial import legendre as Lg
+    g = O.grid(lmax, k=k, layout="dp", thr=0.0)
+    rng = np.random.default_rng(lmax + 7 * k)
+    bl = np.exp(-0.01 * np.arange(lmax + 1) * (np.arange(lmax + 1) + 1))
+    dl = rng.uniform(0.2, 1.0, lmax + 1)
+    th, _, _, _ = _pixel_angles(g)
+    ninv = rng.uniform(0.5, 2.0, g["npix"])
+    ninv[np.abs(0.5 * np.pi - th) < 0.25] = 0.0
+    assert np.any(ninv == 0.0)
+    v = _unit_vectors(g)
+    x = np.clip(v @ v.T, -1.0, 1.0)
+    ell = np.arange(lmax + 1)
+    mask = _tile_mask(g)
+    assert 0 < mask.sum() < mask.size
+    B = np.where(mask, Lg.legval(x, (2 * ell + 1) / (4 * np.pi) * bl), 0.0)
+    D = np.where(mask, Lg.legval(x, (2 * ell + 1) / (4 * np.pi) * dl), 0.0)
+    full = D + B.T @ (ninv[:, None] * B)
+    for band in range(g["nrings"] // k):
+        rings = range(band * k, band * k + k)
+        start = min(int(g["ring_offset"][r]) for r in rings)
+        K = k * int(g["nring"][band * k])
+        idx = start + np.arange(K)
+        M, triples = O.band_block(g, bl, dl, ninv, band)
+        ref = full[np.ix_(idx, idx)]
+        assert triples == int((mask[:, idx].sum(axis=1) ** 2).sum())
+        assert np.max(np.abs(M - ref)) <= 1e-12 * np.max(np.abs(ref)), band
