@@ -131,7 +131,17 @@ void sympix_grid_free(sympix_grid_t grid);
  * separations (one symmetry class per distinct |phi_1 - phi_2|, shared by
  * the transposed and the north/south-mirrored ring pair) and the band width
  * of every block; the host-side plan keeps the block sizes and offsets.
- * Only GREEDY grids (k = 1; one ring per block) can be planned.
+ * On a GREEDY grid (k = 1) a block is one ring.  On a DP grid with
+ * 2 <= k <= 8 a block is one band of k rings (Sec. 2.3 tiling), and the
+ * support is tile adjacency instead of a radius (Sec. 4.2, the locality
+ * approximation): two pixels couple when their k x k tiles lie in bands at
+ * most one apart in latitude and their closed longitude arcs [a/T, (a+1)/T]
+ * of a turn meet, and every two tiles of a polar band couple; r_s is checked
+ * but not used.  Such a plan needs ring0 and ring1 to be multiples of k and
+ * bands of at most 8192 pixels; its blocks are dense (SYMPIX_BLOCK_DENSE,
+ * rows in the band's pixel order, ring_offset - the band's first index), and
+ * sympix_convolve, sympix_support_copy, sympix_table_copy and the calls on
+ * blocks between rings return SYMPIX_EUNSUPPORTED.
  * Allocates the class and kernel tables on the device.  Synchronous.
  * out receives a library-owned handle (free with sympix_plan_free). */
 int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, int ring1,
@@ -214,7 +224,8 @@ int sympix_plan_launches(sympix_plan_t plan, int storage, int sample_precision, 
  * (periodic band including the diagonal; n (n+1) / 2 for dense blocks). */
 int sympix_blocks_size(sympix_plan_t plan, int storage, size_t *bytes, int64_t *elements);
 
-/* Where block (op, ring) sits in the blocks buffer of a storage mode:
+/* Where block (op, ring) sits in the blocks buffer of a storage mode (on a
+ * DP-grid plan `ring` is the band index, ring / k):
  * offset in doubles (a multiple of 4: every block starts on a 32-byte
  * boundary), ring size n, lower band half-width w, format
  * SYMPIX_BLOCK_PBAND or SYMPIX_BLOCK_DENSE.

@@ -87,6 +87,7 @@ using namespace sympix;
 
 extern "C" int sympix_convolve(sympix_plan_t pl, const double *f, int precision, double *g, void *stream) {
     if (!pl || !f || !g) return set_error(SYMPIX_EINVAL, "sympix_convolve: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_convolve: ring blocks only (k = 1)");
     if (precision < SYMPIX_PREC_FP64 || precision > SYMPIX_PREC_FP32X2)
         return set_error(SYMPIX_EINVAL, "sympix_convolve: unknown precision %d", precision);
     if (!pl->table_ready)

@@ -251,6 +251,7 @@ using namespace sympix;
 
 extern "C" int sympix_coupling_size(sympix_plan_t pl, int delta, size_t *bytes, int64_t *elements) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_coupling_size: NULL plan");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_coupling_size: ring blocks only (k = 1)");
     if (delta < 1 || delta >= pl->grid->nrings)
         return set_error(SYMPIX_EINVAL, "sympix_coupling_size: ring offset %d out of [1, nrings)", delta);
     auto it = pl->coupling.find(delta);
@@ -312,6 +313,7 @@ extern "C" int sympix_coupling_size(sympix_plan_t pl, int delta, size_t *bytes, 
 
 extern "C" int sympix_coupling_layout(sympix_plan_t pl, int delta, int op, int ring, int64_t *offset, int32_t *geom) {
     if (!pl || !geom) return set_error(SYMPIX_EINVAL, "sympix_coupling_layout: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_coupling_layout: ring blocks only (k = 1)");
     auto it = pl->coupling.find(delta);
     if (it == pl->coupling.end())
         return set_error(SYMPIX_EINVAL, "sympix_coupling_layout: call sympix_coupling_size(%d) first", delta);
@@ -335,6 +337,7 @@ extern "C" int sympix_coupling_layout(sympix_plan_t pl, int delta, int op, int r
 
 extern "C" int sympix_sample_coupling(sympix_plan_t pl, const double *ninv, int delta, double *out, void *stream) {
     if (!pl || !ninv || !out) return set_error(SYMPIX_EINVAL, "sympix_sample_coupling: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_sample_coupling: ring blocks only (k = 1)");
     auto it = pl->coupling.find(delta);
     if (it == pl->coupling.end())
         return set_error(SYMPIX_EINVAL, "sympix_sample_coupling: call sympix_coupling_size(%d) first", delta);
@@ -358,6 +361,7 @@ extern "C" int sympix_sample_coupling(sympix_plan_t pl, const double *ninv, int 
 extern "C" int sympix_apply(sympix_plan_t pl, int storage, const double *blocks, const int32_t *info, const double *x,
                             double *y, void *stream) {
     if (!pl || !blocks || !info || !x || !y) return set_error(SYMPIX_EINVAL, "sympix_apply: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_apply: ring blocks only (k = 1)");
     if (storage != SYMPIX_STORE_PBAND && storage != SYMPIX_STORE_DENSE)
         return set_error(SYMPIX_EINVAL, "sympix_apply: unknown storage %d", storage);
     if (x == y) return set_error(SYMPIX_EINVAL, "sympix_apply: x and y must not alias");

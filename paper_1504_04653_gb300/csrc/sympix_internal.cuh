@@ -6,6 +6,8 @@
 
 #include <map>
 #include <string>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/sympix.h"
@@ -27,6 +29,22 @@ int cuda_error(cudaError_t e, const char *what);
 // Record a trace event on `st` (no-op unless the plan traces and `st` is not
 // capturing); `name` labels the span since the previous mark, null starts a call.
 void trace_mark(sympix_plan_t pl, cudaStream_t st, const char *name);
+// The canonical form of ring pair (j, rho) of a grid of N rings: a <= b and
+// a <= N-1-b (transposed and north/south-mirrored pairs share kernel values).
+// DP-grid plans (sympix_tiles.cu): the largest |z| of a tile-coupled pixel
+// pair of two ring sizes; the band blocks of bands [g0, g1); their sampler.
+long tile_pair_mmax(int na, int nb, int k, bool all);
+int plan_tile_blocks(sympix_plan_t pl, const std::unordered_map<int64_t, int> &index, int g0, int g1);
+int launch_tiles(sympix_plan_t pl, const double *ninv, int precision, double *blocks, cudaStream_t st);
+inline std::pair<int, int> canon_pair(int N, int j, int rho) {
+    int a = j < rho ? j : rho, b = j < rho ? rho : j;
+    if (a > N - 1 - b) {
+        const int a2 = N - 1 - b, b2 = N - 1 - a;
+        a = a2;
+        b = b2;
+    }
+    return {a, b};
+}
 // columns per chunk of the chunked border solve for width w, and the floats
 // of its per-item scratch (a W x W matrix, the corner sums) for 32 lanes
 int l21_chunk_cols_host(int w);
@@ -171,6 +189,28 @@ struct CanonPair {
     int64_t slot0;  // first slot
 };
 
+// DP grids (k > 1): one dense block per band of k rings, under tile
+// adjacency.  A block's rows are the band's pixels in grid order (pixel c
+// of the band's r-th ring at row c k + r), so tile a (columns a k .. a k +
+// k - 1) is rows a k^2 .. a k^2 + k^2 - 1.
+constexpr int kTileKMax = 8;  // k^2 <= 64 pixels per tile
+struct TileBlock {
+    int32_t op, g;         // operator, band (latitude order, g = ring / k)
+    int32_t K, T;          // rows (k n_g), tiles of the band
+    int32_t k, G;          // tile size, bands of the grid
+    int32_t gnb[3];        // bands g-1, g, g+1 (-1 where none)
+    int32_t Tnb[3];        // their tiles
+    int32_t P[3], Q[3];    // separation-index steps against each (ring of band g first)
+    int32_t par[3], pad;
+    int64_t half[3];       // P Q gcd: z reduced to (-half, half]
+    int64_t off;           // first element of the block (dense K x K, row-major)
+    int64_t meta0;         // first of its 3 k^2 slot bases and 3 k ring offsets
+};
+// One lower tile pair (a2 <= a) of a block with some coupling.
+struct TileItem {
+    int32_t block, a, a2, pad;
+};
+
 // Work item of the sampling launches.
 struct SampleItem {
     int32_t block;
@@ -296,6 +336,15 @@ struct sympix_plan_s {
     // stage): FP64 0 (20.1 ms; 2: 23.4 ms), FP32 3, split FP32 2 (7.9 ms;
     // 1: 30.2 ms).
     int narrow_pref[3] = {0, 3, 2};
+    // DP-grid plans (k > 1): band blocks under tile adjacency
+    bool tiles = false;
+    std::vector<TileBlock> tile_blocks;
+    std::vector<TileItem> tile_items;
+    std::vector<int64_t> tile_slot0;  // per block: [3][k][k] slot of (ring r of g, ring r2 of band d)
+    std::vector<int64_t> tile_noff;   // per block: [3][k] pixel index of column 0 of ring r2 of band d
+    sympix::DevBuf<TileBlock> d_tile_blocks;
+    sympix::DevBuf<TileItem> d_tile_items;
+    sympix::DevBuf<int64_t> d_tile_slot0, d_tile_noff;
     int64_t size_shadow_il = 0, size_l21_il = 0;  // floats
     // device
     sympix::DevBuf<CanonPair> d_pairs;

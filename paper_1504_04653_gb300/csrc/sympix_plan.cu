@@ -156,9 +156,12 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     if (!out) return set_error(SYMPIX_EINVAL, "sympix_support: out is NULL");
     *out = nullptr;
     if (!grid || !r_s) return set_error(SYMPIX_EINVAL, "sympix_support: NULL argument");
-    if (grid->layout != SYMPIX_LAYOUT_GREEDY || grid->k != 1)
-        return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: blocks are planned for k = 1 (greedy) grids only");
     const int N = grid->nrings;
+    // DP grids with k > 1: band blocks under tile adjacency (sympix_tiles.cu)
+    const bool tiles = grid->k > 1;
+    if (tiles && (grid->k > kTileKMax || ring0 % grid->k || ring1 % grid->k))
+        return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: k = %d grids need k <= %d and band-aligned rings",
+                         grid->k, kTileKMax);
     if (nops < 1 || nops > 4096) return set_error(SYMPIX_EINVAL, "sympix_support: nops %d out of [1, 4096]", nops);
     if (ring0 < 0 || ring1 > N || ring0 >= ring1)
         return set_error(SYMPIX_EINVAL, "sympix_support: ring range [%d, %d) not inside [0, %d)", ring0, ring1, N);
@@ -178,6 +181,8 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     pl->ring0 = ring0;
     pl->ring1 = ring1;
     pl->r_s.assign(r_s, r_s + nops);
+    pl->tiles = tiles;
+    pl->all_d = tiles;  // D^ of a band block couples different rings: d at every class
     const std::vector<double> &th = grid->theta;
     const std::vector<int32_t> &nr = grid->nring;
     double hmin = kPi;
@@ -191,17 +196,11 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
 
     // canonical ring pairs met by the planned blocks
     std::unordered_map<int64_t, int> index;
-    auto canon = [&](int j, int rho) {
-        int a = std::min(j, rho), b = std::max(j, rho);
-        if (a > N - 1 - b) {
-            int a2 = N - 1 - b, b2 = N - 1 - a;
-            a = a2;
-            b = b2;
-        }
-        return std::make_pair(a, b);
-    };
+    auto canon = [&](int j, int rho) { return canon_pair(N, j, rho); };
+    const int kk = grid->k;
     for (int j = ring0; j < ring1; ++j)
-        for (int rho = std::max(0, j - rmax); rho <= std::min(N - 1, j + rmax); ++rho) {
+        for (int rho = tiles ? std::max(0, (j / kk - 1) * kk) : std::max(0, j - rmax);
+             rho <= (tiles ? std::min(N - 1, (j / kk + 2) * kk - 1) : std::min(N - 1, j + rmax)); ++rho) {
             auto ab = canon(j, rho);
             int64_t key = (int64_t)ab.first * N + ab.second;
             if (index.count(key)) continue;
@@ -224,7 +223,19 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     int rc;
     DevBuf<double> d_rs, d_margin;
     DevBuf<int32_t> d_mmax;
-    {
+    if (tiles) {  // the largest |z| of a tile-coupled pixel pair; no radius, no threshold
+        pl->pair_mmax.resize((size_t)npairs * nops);
+        pl->margin.assign(nops, INFINITY);
+        std::map<std::pair<int, int>, long> seen;
+        for (int pi = 0; pi < npairs; ++pi) {
+            const CanonPair &cp = pl->pairs[pi];
+            const int ga = cp.a / kk, gb = cp.b / kk;
+            const bool all = ga == gb && (ga == 0 || ga == N / kk - 1);
+            auto key = std::make_pair(all ? -cp.na : cp.na, cp.nb);
+            if (!seen.count(key)) seen[key] = tile_pair_mmax(cp.na, cp.nb, kk, all);
+            for (int o = 0; o < nops; ++o) pl->pair_mmax[(size_t)pi * nops + o] = (int32_t)seen[key];
+        }
+    } else {
         const int tot = npairs * nops;
         if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = d_mmax.alloc((size_t)tot)) ||
             (rc = d_margin.alloc((size_t)tot)))
@@ -274,10 +285,11 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
     k_support_slots<<<(npairs + 127) / 128, 128>>>(npairs, pl->d_pairs.p, grid->d_theta.p, pl->d_slot_u.p,
                                                    pl->d_slot_pair.p);
 
-    // blocks and their coupled neighbour rings
+    // blocks and their coupled neighbour rings (DP grids: one block per band)
+    if (tiles && (rc = plan_tile_blocks(pl, index, ring0 / kk, ring1 / kk))) return fail(rc);
     const int nb = ring1 - ring0;
     int64_t offp = 0, offd = 0;
-    for (int o = 0; o < nops; ++o) {
+    for (int o = 0; o < (tiles ? 0 : nops); ++o) {
         for (int j = ring0; j < ring1; ++j) {
             BlockDesc bd{};
             bd.op = o;
@@ -347,13 +359,15 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             pl->blocks.push_back(bd);
         }
     }
-    pl->size_pband = offp;
-    pl->size_dense = offd;
+    if (!tiles) {
+        pl->size_pband = offp;
+        pl->size_dense = offd;
+    }
 
     // sampling work items: pband blocks in tiles of 128 columns, bucketed by
     // band width; dense blocks of up to 64 pixels in tiles of 8 elements (a
     // warp each), larger ones in tiles of 256 (a thread each)
-    for (size_t b = 0; b < pl->blocks.size(); ++b) {
+    for (size_t b = 0; b < (tiles ? 0 : pl->blocks.size()); ++b) {
         const BlockDesc &bd = pl->blocks[b];
         if (bd.format == SYMPIX_BLOCK_PBAND) {
             int bucket = bd.w <= 8 ? 0 : bd.w <= 16 ? 1 : bd.w <= 32 ? 2 : 3;
@@ -367,7 +381,7 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         }
     }
     // convolution work items: every block's ring in tiles of 128 pixels
-    for (size_t b = 0; b < pl->blocks.size(); ++b) {
+    for (size_t b = 0; b < (tiles ? 0 : pl->blocks.size()); ++b) {
         const BlockDesc &bd = pl->blocks[b];
         for (int q0 = 0; q0 < bd.n; q0 += 128)
             pl->items_conv.push_back({(int32_t)b, q0, grid->offset[bd.ring], grid->stride[bd.ring], 0});
@@ -569,6 +583,9 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
         (rc = pl->d_shadow.alloc((pl->factor_items[5].empty() && pl->chol_items.empty())
                                      ? 1
                                      : std::max<int64_t>(pl->size_pband, 1))))
+        return fail(rc);
+    if (tiles && ((rc = pl->d_tile_blocks.upload(pl->tile_blocks)) || (rc = pl->d_tile_items.upload(pl->tile_items)) ||
+                  (rc = pl->d_tile_slot0.upload(pl->tile_slot0)) || (rc = pl->d_tile_noff.upload(pl->tile_noff))))
         return fail(rc);
     if ((rc = pl->d_blocks.upload(pl->blocks)) || (rc = pl->d_entries.upload(pl->entries)) ||
         (rc = pl->d_items_dense.upload(pl->items_dense)) || (rc = pl->d_items_dense_rows.upload(pl->items_dense_rows)) || (rc = pl->d_items_conv.upload(pl->items_conv)))
@@ -799,6 +816,7 @@ extern "C" int sympix_plan_launches(sympix_plan_t pl, int storage, int sample_pr
         *table = 1 + (pl->nslots > 0 ? chunks : 0);
     }
     int s = sample_precision != SYMPIX_PREC_FP64 ? 1 : 0;  // the N^-1 split
+    s += pl->tile_items.empty() ? 0 : 1;                     // band blocks of a DP grid
     for (int b = 0; b < 4; ++b) s += pl->items_pband[b].empty() ? 0 : 1;
     s += pl->items_dense.empty() ? 0 : 1;
     s += pl->items_dense_rows.empty() ? 0 : 1;
@@ -878,9 +896,11 @@ extern "C" int sympix_blocks_size(sympix_plan_t pl, int storage, size_t *bytes, 
 extern "C" int sympix_block_layout(sympix_plan_t pl, int storage, int op, int ring, int64_t *offset, int32_t *n,
                                    int32_t *w, int32_t *format) {
     if (!pl) return set_error(SYMPIX_EINVAL, "sympix_block_layout: NULL plan");
-    if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1)
+    // DP-grid plans: `ring` is the band index (one block per band of k rings)
+    const int kk = pl->tiles ? pl->grid->k : 1, lo = pl->ring0 / kk, hi = pl->ring1 / kk;
+    if (op < 0 || op >= pl->nops || ring < lo || ring >= hi)
         return set_error(SYMPIX_EINVAL, "sympix_block_layout: (op %d, ring %d) not planned", op, ring);
-    const BlockDesc &bd = pl->blocks[(size_t)op * (pl->ring1 - pl->ring0) + (ring - pl->ring0)];
+    const BlockDesc &bd = pl->blocks[(size_t)op * (hi - lo) + (ring - lo)];
     const bool pb = storage == SYMPIX_STORE_PBAND;
     if (offset) *offset = pb ? bd.off_pband : bd.off_dense;
     if (n) *n = bd.n;
@@ -933,6 +953,7 @@ extern "C" int sympix_plan_device_bytes(sympix_plan_t pl, size_t *bytes, size_t 
 
 extern "C" int sympix_support_copy(sympix_plan_t pl, int op, int ring, int radius, int32_t *mmax) {
     if (!pl || !mmax) return set_error(SYMPIX_EINVAL, "sympix_support_copy: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_support_copy: ring blocks only (k = 1)");
     if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1 || radius < 0)
         return set_error(SYMPIX_EINVAL, "sympix_support_copy: (op %d, ring %d) not planned", op, ring);
     for (int i = 0; i <= 2 * radius; ++i) mmax[i] = -1;

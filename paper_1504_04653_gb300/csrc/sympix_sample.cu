@@ -183,6 +183,13 @@ extern "C" int sympix_sample_blocks(sympix_plan_t pl, const double *ninv, int pr
         k_split_ninv<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ninv, pl->d_ninv32.p, pl->d_ninvlo.p);
         trace_mark(pl, st, "k_split_ninv");
     }
+    if (pl->tiles) {  // band blocks of a DP grid
+        int rc = launch_tiles(pl, ninv, precision, blocks, st);
+        if (rc) return rc;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "sympix_sample_blocks: launch");
+        return SYMPIX_OK;
+    }
     if (precision == SYMPIX_PREC_FP64) {
         dense ? launch_pband<0, true>(pl, ninv, blocks, st) : launch_pband<0, false>(pl, ninv, blocks, st);
     } else if (precision == SYMPIX_PREC_FP32) {

@@ -185,6 +185,7 @@ extern "C" int sympix_kernel_table(sympix_plan_t pl, const double *bl, const dou
 
 extern "C" int sympix_table_copy(sympix_plan_t pl, int op, int ring, int rho, int count, double *b, double *d) {
     if (!pl || !b) return set_error(SYMPIX_EINVAL, "sympix_table_copy: NULL argument");
+    if (pl->tiles) return set_error(SYMPIX_EUNSUPPORTED, "sympix_table_copy: ring blocks only (k = 1)");
     if (op < 0 || op >= pl->nops || ring < pl->ring0 || ring >= pl->ring1)
         return set_error(SYMPIX_EINVAL, "sympix_table_copy: (op %d, ring %d) not planned", op, ring);
     const BlockDesc &bd = pl->blocks[(size_t)op * (pl->ring1 - pl->ring0) + (ring - pl->ring0)];

@@ -186,7 +186,13 @@ class Plan:
 
     @property
     def nblocks(self) -> int:
-        return self.nops * (self.ring1 - self.ring0)
+        """Blocks per storage: one per (operator, ring), or on a DP grid with
+        k > 1 one per (operator, band of k rings)."""
+        return self.nops * (self.ring1 - self.ring0) // self.k
+
+    @property
+    def k(self) -> int:
+        return self.grid.k
 
     def blocks_size(self, storage="pband"):
         b, e = ctypes.c_size_t(), ctypes.c_int64()
