@@ -138,7 +138,7 @@ void sympix_grid_free(sympix_grid_t grid);
  * most one apart in latitude and their closed longitude arcs [a/T, (a+1)/T]
  * of a turn meet, and every two tiles of a polar band couple; r_s is checked
  * but not used.  Such a plan needs ring0 and ring1 to be multiples of k and
- * bands of at most 8192 pixels; its blocks are dense (SYMPIX_BLOCK_DENSE,
+ * bands of at most 16384 pixels; its blocks are dense (SYMPIX_BLOCK_DENSE,
  * rows in the band's pixel order, ring_offset - the band's first index), and
  * sympix_convolve, sympix_support_copy, sympix_table_copy and the calls on
  * blocks between rings return SYMPIX_EUNSUPPORTED.

@@ -100,8 +100,8 @@ int plan_tile_blocks(sympix_plan_t pl, const std::unordered_map<int64_t, int> &i
         for (int g = g0; g < g1; ++g) {
             const int n = nr[g * k];
             const int64_t K = (int64_t)k * n;
-            if (K > 8192)
-                return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: band %d has %lld pixels, above 8192", g,
+            if (K > 16384)
+                return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: band %d has %lld pixels, above 16384", g,
                                  (long long)K);
             TileBlock tb{};
             tb.op = o;

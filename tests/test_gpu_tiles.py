@@ -99,6 +99,30 @@ def test_band_blocks_lmax127_k8(S):
         assert _err(M, ref) <= TOL["fp64"], g
 
 
+def test_band_blocks_lmax500_k8(S):
+    """l_max = 500, k = 8 (64 bands, the equatorial ones of 8640 pixels):
+    the polar band, a mid-latitude band and the band next to the equator
+    against the oracle; only those blocks leave the device."""
+    import torch
+    lmax, k = 500, 8
+    og = _oracle_grid(lmax, k)
+    nb = og["nrings"] // k
+    grid = S.Grid(lmax, k=k, layout="dp", polar_thr=0.0)
+    wl = _workload(lmax, k)
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    ninv = wl.ninv(colat)
+    S.sympix_kernel_table(plan, torch.tensor(wl.beams(), device="cuda"), torch.tensor(wl.priors(), device="cuda"))
+    blocks = S.sympix_sample_blocks(plan, torch.tensor(ninv, device="cuda"), precision="fp64")
+    for g in (0, 20, nb // 2 - 1):
+        off, n, _, fmt = plan.block_layout("pband", 0, g)
+        assert fmt == S.BLOCK_DENSE and n == k * og["nring"][g * k]
+        M = blocks[off:off + n * n].reshape(n, n).cpu().numpy()
+        ref, _ = O.band_block(og, wl.beams()[0], wl.priors()[0], ninv[0], g)
+        assert _err(M, ref) <= TOL["fp64"], (g, _err(M, ref))
+    assert n == 8640
+
+
 def test_band_factor_matches_oracle(S):
     """The FP64 factor of every band block at l_max = 31, k = 2.  A band
     whose rings hold more than 2 l_max + 1 pixels carries a band-limited D^
