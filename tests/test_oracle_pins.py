@@ -720,3 +720,43 @@ def test_band_block_matches_dense_brute_force(lmax, k):
         ref = full[np.ix_(idx, idx)]
         assert triples == int((mask[:, idx].sum(axis=1) ** 2).sum())
         assert np.max(np.abs(M - ref)) <= 1e-12 * np.max(np.abs(ref)), band
+
+
+def _first_tile_ratio(lmax, k):
+    """Table sample_benchmark's ratio under the reading 'b is evaluated for the
+    first tile of each band only': (ordered tile-coupled pixel pairs) /
+    (pairs of the first tile of every band with its coupled pixels), on the
+    DP grid with the paper's polar threshold."""
+    g = O.grid(lmax, k=k, layout="dp")
+    nb = g["nrings"] // (2 * k)
+    T = [int(g["nring"][i * k]) // k for i in range(nb)]
+    Tg = T + T[::-1]
+    num = den = 0
+    for gi in range(len(Tg)):
+        for gj in (gi - 1, gi, gi + 1):
+            if not 0 <= gj < len(Tg):
+                continue
+            Ta, Tb = Tg[gi], Tg[gj]
+            if gi == gj and gi in (0, len(Tg) - 1):
+                cnt = np.full(Ta, Tb)
+            else:
+                a = np.arange(Ta)
+                lo = -((-a * Tb) // Ta) - 1
+                hi = ((a + 1) * Tb) // Ta
+                cnt = np.minimum(Tb, hi - lo + 1)
+            num += int(cnt.sum()) * k ** 4
+            den += int(cnt[0]) * k ** 4
+    return num / den
+
+
+def test_tile_evaluation_count_reading():
+    """The paper does not spell out how Table sample_benchmark counts (parity
+    unpinned).  Under the reading above the ratio grows like l_max, as the
+    table's does, and lands within a factor 1.5 of the table's 149, 335 and
+    732 at l_max 750, 1500 and 3000 (k = 8); the small-l_max rows differ by
+    ~2x, where the polar bands dominate."""
+    table = {750: 149, 1500: 335, 3000: 732}
+    got = {l: _first_tile_ratio(l, 8) for l in table}
+    for l, want in table.items():
+        assert want / 1.5 <= got[l] <= want * 1.5, (l, got[l], want)
+    assert 1.7 <= got[3000] / got[1500] <= 2.3
