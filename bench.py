@@ -5,8 +5,9 @@ A step is one pass of the whole hot path over one operator at l_max = 3000,
 FWHM 5': kernel table (FP64) -> block sampling D^ + B^T N^-1 B^ -> Cholesky
 of every block.  The headline `value` is the mixed path (FP32 contraction,
 FP32 factor with FP64 rescue); the FP64 and split-FP32 arms are timed beside
-it, and two further workloads (l_max = 1500 with an FP64 factor, and 32
-operators at l_max = 1000) are timed as sub-lines under "configs".
+it, and further workloads (l_max = 1500 with an FP64 factor, 32 operators at
+l_max = 1000, and the band blocks of the paper's DP grid at l_max = 500,
+k = 8) are timed as sub-lines under "configs".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -828,6 +829,59 @@ def coupling_timing(S, P, args, hbm, pk):
     return ent
 
 
+def dp_timing(S, W, args, hbm, pk, lmax=500, k=8):
+    """The paper's DP grid with k x k tiles (f2): one block per band of k rings
+    under tile adjacency, l_max = 500, k = 8 (64 bands of up to 8640
+    pixels), one operator with a beam narrower than a tile.  Times the kernel
+    table and the band-block sampling (FP64 and FP32) with CUDA events on
+    the stream, L2 flushed before each; the dense factor of these bands (one
+    CTA per band) is not timed."""
+    import torch
+    grid = S.Grid(lmax, k=k, layout="dp", polar_thr=0.0)
+    fwhm = 60.0 * 180.0 / lmax * k / 4.0
+    wl = W.Workload(f"dp_lmax{lmax}_k{k}", lmax, [fwhm], [20.0], [41])
+    plan = S.Plan(grid, wl.radii())
+    colat = W.pixel_colatitude(grid.theta, grid.nring, grid.ring_offset, grid.ring_stride, grid.npix)
+    bl = torch.tensor(wl.beams(), device="cuda")
+    dl = torch.tensor(wl.priors(), device="cuda")
+    ninv = torch.tensor(wl.ninv(colat), device="cuda")
+    nb = plan.nblocks
+    stored = sum(plan.block_layout("pband", 0, g)[1] ** 2 for g in range(nb))
+    nbytes, _ = plan.blocks_size("pband")
+    out = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    reps = max(2, min(args.steps, 5))
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    ent = {"workload": wl.name, "lmax": lmax, "k": k, "npix": int(grid.npix), "bands": nb,
+           "largest_band": int(max(plan.block_layout("pband", 0, g)[1] for g in range(nb))),
+           "stored_elements": int(stored), "table_slots": int(plan.nslots),
+           "multiply_adds": int(plan.ntriples)}
+    ent["table_ms"] = timed(lambda: S.sympix_kernel_table(plan, bl, dl))
+    for prec in ("fp64", "fp32"):
+        ms = timed(lambda: S.sympix_sample_blocks(plan, ninv, precision=prec, out=out))
+        model = {"k_sample_tiles": (8.0 * stored, 2.0 * plan.ntriples, prec)}
+        r = roofline("k_sample_tiles", ms, model, hbm, pk)
+        r.update({"elements_per_s": stored / (ms * 1e-3), "note": "includes zeroing the blocks buffer"})
+        ent[prec] = r
+    del out, flush
+    torch.cuda.empty_cache()
+    return ent
+
+
 def sub_configs(S, W, args, dev, stream, flush, hbm, pk):
     """Two more workloads, each timed the same way (graph replay, L2 flushed,
     CUDA events): l_max = 1500 with an FP64 factor after the mixed and the
@@ -854,6 +908,7 @@ def sub_configs(S, W, args, dev, stream, flush, hbm, pk):
         out[key] = ent
         del P
         torch.cuda.empty_cache()
+    out["dp_lmax500_k8"] = dp_timing(S, W, args, hbm, pk)
     return out
 
 

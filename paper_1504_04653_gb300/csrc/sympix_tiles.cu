@@ -100,7 +100,7 @@ int plan_tile_blocks(sympix_plan_t pl, const std::unordered_map<int64_t, int> &i
         for (int g = g0; g < g1; ++g) {
             const int n = nr[g * k];
             const int64_t K = (int64_t)k * n;
-            if (K > 16384)
+            if (K > 16384)  // also keeps every separation index z of the sampler within 32 bits
                 return set_error(SYMPIX_EUNSUPPORTED, "sympix_support: band %d has %lld pixels, above 16384", g,
                                  (long long)K);
             TileBlock tb{};
@@ -170,8 +170,25 @@ int plan_tile_blocks(sympix_plan_t pl, const std::unordered_map<int64_t, int> &i
                         for (long t = 0; t < ca; ++t) mates.insert((la + t) % tb.T);
                     }
                 }
-                for (long a2 : mates)
-                    if (a2 <= a) pl->tile_items.push_back({bi, (int32_t)a, (int32_t)a2, 0});
+                for (long a2 : mates) {
+                    if (a2 > a) continue;
+                    pl->tile_items.push_back({bi, (int32_t)a, (int32_t)a2, 0});
+                    // work of the item: k^2 x k^2 multiply-adds per pixel of a
+                    // common tile (k^2 pixels), two gathered products per pixel pair
+                    int64_t common = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        if (tb.gnb[d] < 0) continue;
+                        const bool all = tb.gnb[d] == g && polar;
+                        long l1, c1, l2, c2;
+                        tile_range(a, tb.T, tb.Tnb[d], all, &l1, &c1);
+                        tile_range(a2, tb.T, tb.Tnb[d], all, &l2, &c2);
+                        for (long i = 0; i < c1; ++i)
+                            if (((l1 + i) % tb.Tnb[d] - l2 + tb.Tnb[d]) % tb.Tnb[d] < c2) ++common;
+                    }
+                    const int64_t k2 = (int64_t)k * k;
+                    pl->ntriples += common * k2 * k2 * k2;
+                    pl->nmults += common * 2 * k2 * k2;
+                }
             }
             pl->tile_blocks.push_back(tb);
         }
@@ -217,33 +234,41 @@ struct TileSrcF2 {
     __device__ static double out(V x) { return elem_to_f64(x); }
 };
 
+// z = (2c+1) Q - (2p+1) P of pixels c < n_a, p < n_b lies in (-2 half,
+// 2 half) (half = n_a n_b / g), so one correction reduces it to
+// (-half, half].
+__device__ __forceinline__ int reduce_z_near(int z, int half) {
+    return z > half ? z - 2 * half : (z <= -half ? z + 2 * half : z);
+}
+
 // One CTA per lower tile pair (a, a2) of a band block: the k^2 x k^2 tile
 // of rows a and columns a2 (and its transpose), summed over the pixels p of
 // every tile coupled to both, one such tile at a time: Ba[p][i] =
 // b(p, row i) N^-1_p and Bb[p][j] = b(p, column j) are gathered from the
-// class table into shared memory, then each thread adds a 4 x 4 piece of
-// Ba^T Bb.
-template <class S>
+// class table into shared memory, then each of the 16 x 16 threads adds an
+// MU x MU piece of Ba^T Bb (MU = ceil(k^2 / 16)).  Band sizes stay below
+// 2^15 pixels, so every z fits 32 bits.
+template <class S, int K>
 __global__ void __launch_bounds__(256) k_sample_tiles(const TileItem *__restrict__ items,
                                                       const TileBlock *__restrict__ tbs,
                                                       const int64_t *__restrict__ slot0s,
                                                       const int64_t *__restrict__ noffs, int64_t nslots,
                                                       int64_t npix, S src, double *__restrict__ out) {
     typedef typename S::V V;
+    constexpr int KK = K * K, MU = (KK + 15) / 16;
     extern __shared__ __align__(16) unsigned char tile_smem[];
+    V *Ba = reinterpret_cast<V *>(tile_smem), *Bb = Ba + KK * KK;  // [p][row], [p][column]
     const TileItem it = items[blockIdx.x];
     const TileBlock tb = tbs[it.block];
-    const int k = tb.k, kk = k * k;
-    V *Ba = reinterpret_cast<V *>(tile_smem), *Bb = Ba + kk * kk;  // [p][row], [p][column]
     const int64_t tbase = (int64_t)tb.op * nslots, nbase = (int64_t)tb.op * npix;
     const int64_t *slot0 = slot0s + tb.meta0;
-    const int64_t *noff = noffs + tb.meta0 / k;  // 3 k^2 slots, 3 k offsets per block
+    const int64_t *noff = noffs + tb.meta0 / K;  // 3 k^2 slots, 3 k offsets per block
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    V acc[4][4];
+    V acc[MU][MU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < MU; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = V(0);
+        for (int v = 0; v < MU; ++v) acc[u][v] = V(0);
     const bool polar = tb.g == 0 || tb.g == tb.G - 1;
     for (int d = 0; d < 3; ++d) {
         if (tb.gnb[d] < 0) continue;
@@ -252,74 +277,91 @@ __global__ void __launch_bounds__(256) k_sample_tiles(const TileItem *__restrict
         long l1, c1, l2, c2;
         tile_range(it.a, tb.T, Td, all, &l1, &c1);
         tile_range(it.a2, tb.T, Td, all, &l2, &c2);
-        const long P = tb.P[d], Q = tb.Q[d], half = tb.half[d];
-        const int par = tb.par[d];
+        const int P = tb.P[d], Q = tb.Q[d], half = (int)tb.half[d], par = tb.par[d];
         for (long i1 = 0; i1 < c1; ++i1) {
-            const long b = (l1 + i1) % Td;
-            if ((b - l2 + Td) % Td >= c2) continue;  // not coupled to tile a2
+            long b = l1 + i1;
+            if (b >= Td) b -= Td;
+            long rel = b - l2;
+            if (rel < 0) rel += Td;
+            if (rel >= c2) continue;  // not coupled to tile a2
             __syncthreads();
-            for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) {
-                const int pi = e / kk, qi = e % kk;
-                const int r2 = pi % k, r = qi % k;
-                const long cp = b * k + pi / k;
-                const long ca = (long)it.a * k + qi / k, cb = (long)it.a2 * k + qi / k;
-                const V nv = src.n(nbase + noff[d * k + r2] + cp * k);
-                long za = reduce_z((2 * ca + 1) * Q - (2 * cp + 1) * P, half);
-                long zb = reduce_z((2 * cb + 1) * Q - (2 * cp + 1) * P, half);
+            for (int e = threadIdx.x; e < KK * KK; e += 256) {
+                const int pi = e / KK, qi = e % KK;
+                const int r2 = pi % K, r = qi % K;
+                const int cp = (int)b * K + pi / K;
+                const int ca = it.a * K + qi / K, cb = it.a2 * K + qi / K;
+                const V nv = src.n(nbase + noff[d * K + r2] + (int64_t)cp * K);
+                int za = reduce_z_near((2 * ca + 1) * Q - (2 * cp + 1) * P, half);
+                int zb = reduce_z_near((2 * cb + 1) * Q - (2 * cp + 1) * P, half);
                 za = za < 0 ? -za : za;
                 zb = zb < 0 ? -zb : zb;
-                const int64_t s0 = tbase + slot0[(d * k + r) * k + r2];
-                Ba[pi * kk + qi] = S::mul(src.tb(s0 + ((za - par) >> 1)), nv);
-                Bb[pi * kk + qi] = src.tb(s0 + ((zb - par) >> 1));
+                const int64_t s0 = tbase + slot0[(d * K + r) * K + r2];
+                Ba[pi * KK + qi] = S::mul(src.tb(s0 + ((za - par) >> 1)), nv);
+                Bb[pi * KK + qi] = src.tb(s0 + ((zb - par) >> 1));
             }
             __syncthreads();
-            for (int pi = 0; pi < kk; ++pi) {
-                V x[4], y[4];
+#pragma unroll 4
+            for (int pi = 0; pi < KK; ++pi) {
+                V x[MU], y[MU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    x[u] = 4 * ty + u < kk ? Ba[pi * kk + 4 * ty + u] : V(0);
-                    y[u] = 4 * tx + u < kk ? Bb[pi * kk + 4 * tx + u] : V(0);
+                for (int u = 0; u < MU; ++u) {
+                    x[u] = MU * ty + u < KK ? Ba[pi * KK + MU * ty + u] : V(0);
+                    y[u] = MU * tx + u < KK ? Bb[pi * KK + MU * tx + u] : V(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < MU; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = S::fma_(x[u], y[v], acc[u][v]);
+                    for (int v = 0; v < MU; ++v) acc[u][v] = S::fma_(x[u], y[v], acc[u][v]);
             }
         }
     }
     // D^ where the two tiles are neighbours (same band: a2 = a, a +- 1, or any in a polar band)
     long ld, cd;
     tile_range(it.a, tb.T, tb.T, polar, &ld, &cd);
-    const bool dcoup = (it.a2 - ld + tb.T) % tb.T < cd;
-    const int64_t K = tb.K;
+    long rel = it.a2 - ld;
+    if (rel < 0) rel += tb.T;
+    const bool dcoup = rel < cd;
+    const int64_t Kr = tb.K;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < MU; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int i = 4 * ty + u, j = 4 * tx + v;
-            if (i >= kk || j >= kk) continue;
+        for (int v = 0; v < MU; ++v) {
+            const int i = MU * ty + u, j = MU * tx + v;
+            if (i >= KK || j >= KK) continue;
             V val = acc[u][v];
             if (dcoup) {
-                const long ci = (long)it.a * k + i / k, cj = (long)it.a2 * k + j / k;
-                long z = reduce_z(2 * (ci - cj), tb.half[1]);
+                const int ci = it.a * K + i / K, cj = it.a2 * K + j / K;
+                int z = reduce_z_near(2 * (ci - cj), (int)tb.half[1]);
                 z = z < 0 ? -z : z;
-                val = S::add(val, src.td(tbase + slot0[(k + i % k) * k + j % k] + (z >> 1)));
+                val = S::add(val, src.td(tbase + slot0[(K + i % K) * K + j % K] + (z >> 1)));
             }
-            const int64_t row = (int64_t)it.a * kk + i, col = (int64_t)it.a2 * kk + j;
+            const int64_t row = (int64_t)it.a * KK + i, col = (int64_t)it.a2 * KK + j;
             const double w = S::out(val);
-            out[tb.off + row * K + col] = w;
-            if (it.a != it.a2) out[tb.off + col * K + row] = w;
+            out[tb.off + row * Kr + col] = w;
+            if (it.a != it.a2) out[tb.off + col * Kr + row] = w;
         }
+}
+
+template <class S, int K>
+static void launch_tiles_k(sympix_plan_t pl, S src, double *blocks, cudaStream_t st) {
+    const size_t smem = (size_t)2 * K * K * K * K * sizeof(typename S::V);
+    cudaFuncSetAttribute(k_sample_tiles<S, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sample_tiles<S, K><<<(unsigned)pl->tile_items.size(), 256, smem, st>>>(
+        pl->d_tile_items.p, pl->d_tile_blocks.p, pl->d_tile_slot0.p, pl->d_tile_noff.p, pl->nslots, pl->grid->npix,
+        src, blocks);
 }
 
 template <class S>
 static void launch_tiles_with(sympix_plan_t pl, S src, double *blocks, cudaStream_t st) {
-    const int k = pl->grid->k;
-    const size_t smem = (size_t)2 * k * k * k * k * sizeof(typename S::V);
-    cudaFuncSetAttribute(k_sample_tiles<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sample_tiles<S><<<(unsigned)pl->tile_items.size(), 256, smem, st>>>(
-        pl->d_tile_items.p, pl->d_tile_blocks.p, pl->d_tile_slot0.p, pl->d_tile_noff.p, pl->nslots, pl->grid->npix,
-        src, blocks);
+    switch (pl->grid->k) {
+    case 2: launch_tiles_k<S, 2>(pl, src, blocks, st); break;
+    case 3: launch_tiles_k<S, 3>(pl, src, blocks, st); break;
+    case 4: launch_tiles_k<S, 4>(pl, src, blocks, st); break;
+    case 5: launch_tiles_k<S, 5>(pl, src, blocks, st); break;
+    case 6: launch_tiles_k<S, 6>(pl, src, blocks, st); break;
+    case 7: launch_tiles_k<S, 7>(pl, src, blocks, st); break;
+    default: launch_tiles_k<S, 8>(pl, src, blocks, st); break;
+    }
 }
 
 // Zeroes the blocks, then writes every tile pair with some coupling.
