@@ -170,7 +170,7 @@ int sympix_support(sympix_grid_t grid, int nops, const double *r_s, int ring0, i
                                           kernel of 1 where they cannot all be resident),
                                           9 <= w <= 12 as 2 beside it (3: FP64 and split FP32
                                           as 2); -1 (default) per
-                                          arithmetic, as measured at l_max 3000: FP64 0, FP32 3,
+                                          arithmetic, as measured at l_max 3000: FP64 2, FP32 3,
                                           split FP32 2.  sympix_autotune times the candidates for
                                           its factor arithmetic */
 #define SYMPIX_OPT_WAIT_LIMIT 5       /* polls of a bounded device wait (default 2^22, about

@@ -78,25 +78,41 @@ __global__ void __launch_bounds__(32) k_f32_band_pass(const F32Slice *__restrict
 }
 
 // Band pass on an FP64 (V = double) or split-FP32 (V = DF) shadow, widths
-// up to 12: one warp per slice, one lane per block; info = i + 1 for the
-// first row whose pivot is not positive (the border kernels then leave the
-// block alone).
+// up to 12: one CTA of four warps per slice, one lane per block; from w = 4
+// the four warps share each block's window (band_lanes4), below it warp 0
+// runs the one-warp loop alone.  info = i + 1 for the first row whose pivot
+// is not positive (the border kernels then leave the block alone).
+template <class V, int W>
+__device__ __forceinline__ int exact_band_w(V *shs, int lane, int m, int mmax, unsigned char *smem) {
+    if constexpr (W >= 4) {
+        return band_lanes4_any<V, W>(shs, lane, m, mmax, smem);
+    } else {
+        if (threadIdx.x >= 32) return 0;
+        return band_lanes_loop<V, W>(shs, lane, m, mmax, reinterpret_cast<V *>(smem));
+    }
+}
+
 template <class V>
-__global__ void __launch_bounds__(32) k_exact_band_pass(const F32Slice *__restrict__ slices,
-                                                        const int32_t *__restrict__ items,
-                                                        const BlockDesc *__restrict__ blocks, V *__restrict__ sh,
-                                                        int32_t *__restrict__ info) {
+__global__ void __launch_bounds__(128) k_exact_band_pass(const F32Slice *__restrict__ slices,
+                                                         const int32_t *__restrict__ items,
+                                                         const BlockDesc *__restrict__ blocks, V *__restrict__ sh,
+                                                         int32_t *__restrict__ info) {
     extern __shared__ __align__(16) unsigned char exact_smem[];
-    V *stage = reinterpret_cast<V *>(exact_smem);
     const F32Slice sl = slices[blockIdx.x];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     int m = 0, bi = -1;
     if (lane < sl.count) {
         bi = items[sl.first + lane];
         m = blocks[bi].n - sl.w;
     }
-    const int r = ExactBandDispatch<12, V>::run(sl.w, sh + sl.sh, lane, m, sl.rows - sl.w, stage);
-    if (bi >= 0) info[bi] = r;
+    V *shs = sh + sl.sh;
+    const int mmax = sl.rows - sl.w;
+    int r = 0;
+    StaticFor<0, 13>::run([&](auto Wc) {
+        constexpr int W = decltype(Wc)::value;
+        if (sl.w == W) r = exact_band_w<V, W>(shs, lane, m, mmax, exact_smem);
+    });
+    if (bi >= 0 && threadIdx.x < 32) info[bi] = r;
 }
 
 // The factor back to the FP64 blocks: L11 rows from the band shadow and
@@ -263,9 +279,9 @@ static void launch_exact_slices(sympix_plan_t pl, double *blocks, int32_t *info,
         k_f32_shadow_in<V><<<(unsigned)nin, 256, 0, st>>>(pl->d_f32_tiles_lo.p, sl, pl->d_f32_items.p, pl->d_blocks.p,
                                                           blocks, sh);
         trace_mark(pl, st, "k_f32_shadow_in");
-        const size_t smem = (size_t)2 * 13 * 13 * 32 * sizeof(V);
+        const size_t smem = band4_smem<V, 12>();  // >= the one-warp loop's two periods of w = 3
         cudaFuncSetAttribute(k_exact_band_pass<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_exact_band_pass<V><<<(unsigned)nf, 32, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, sh, info);
+        k_exact_band_pass<V><<<(unsigned)nf, 128, smem, st>>>(sl, pl->d_f32_items.p, pl->d_blocks.p, sh, info);
         trace_mark(pl, st, std::is_same<V, double>::value ? "k_f64_band_pass" : "k_df_band_pass");
         if constexpr (std::is_same<V, double>::value)
             launch_f64_l21(pl, blocks, info, st);

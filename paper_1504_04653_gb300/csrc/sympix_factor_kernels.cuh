@@ -131,7 +131,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 template <int B, int E>
 struct StaticFor {
     template <class F>
-    __device__ __forceinline__ static void run(F &f) {
+    __device__ __forceinline__ static void run(F &&f) {
         f(std::integral_constant<int, B>{});
         StaticFor<B + 1, E>::run(f);
     }
@@ -139,7 +139,7 @@ struct StaticFor {
 template <int E>
 struct StaticFor<E, E> {
     template <class F>
-    __device__ __forceinline__ static void run(F &) {}
+    __device__ __forceinline__ static void run(F &&) {}
 };
 
 // Band pass of one block in one lane, exact width W.
@@ -415,6 +415,162 @@ __device__ __forceinline__ int band_lanes_loop(T *shs, int lane, int m, int mmax
     }
     cp_async_wait<0>();
     return info;
+}
+
+// The band pass of the exact arithmetics over the four schedulers of an SM:
+// four warps per slice, each lane still one block.  A warp's FP64 or
+// split-FP32 instructions issue on its own scheduler only (a DFMA costs that
+// scheduler 64 cycles whatever the other warps do), so one warp per slice
+// leaves three quarters of the SM idle and every step's whole chain on one
+// pipe.  Here the window's entries are dealt out by diagonal: Wn[r][c] with
+// r - c = delta belongs to warp band4_owner(W, delta).  The window's shift
+// moves each entry along its own diagonal, so ownership never changes and
+// each warp keeps its entries in registers.  Per step:
+//   A. the owner of diagonal delta >= 1 forms l[delta] = Wn[delta][0] rs
+//      (and stores it as L); warp 0 (the main diagonal) stores L's diagonal;
+//   B. every warp reads l from shared memory and updates its entries;
+//      warp 0 first forms the next pivot Wn[1][1] - l1^2 and its rsqrt;
+//      then the shift, and the entering row's entries of each diagonal.
+// Named barrier 1 (all 128 threads) separates A and B and the steps.  Same
+// operations per entry, in the same order, as band_lanes_loop.
+__host__ __device__ constexpr int band4_owner(int W, int delta) {
+    if (delta == 0) return 0;
+    int load[4] = {0, 0, 0, 0};
+    int own = 1;
+    for (int d = 1; d <= W; ++d) {  // most entries first (diagonal d has W - d + 1)
+        int best = 1;
+        for (int q = 2; q < 4; ++q)
+            if (load[q] < load[best]) best = q;
+        load[best] += W - d + 1;
+        if (d == delta) own = best;
+    }
+    return own;
+}
+
+__device__ __forceinline__ void band4_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
+
+// Shared memory of band_lanes4: the staging of band_lanes_loop, then l[W+1][32],
+// rs[32] and the lanes' failure flags.
+template <class T, int W>
+constexpr size_t band4_smem() {
+    return (size_t)(2 * (W + 1) * (W + 1) * 32 + (W + 1) * 32 + 32) * sizeof(T) + 32 * sizeof(int);
+}
+
+template <class T, int W, int Q>
+__device__ __forceinline__ int band_lanes4(T *shs, int lane, int m, int mmax, unsigned char *smem) {
+    constexpr int RL = W + 1, CH = RL * RL;
+    constexpr int PER16 = 16 / (int)sizeof(T);
+    T *stage = reinterpret_cast<T *>(smem);
+    T *ls = stage + 2 * CH * 32;  // l[delta][lane]
+    T *rss = ls + RL * 32;        // rs[lane]
+    int *bads = reinterpret_cast<int *>(rss + 32);
+    const int tid = Q * 32 + lane;
+    T *band = shs + lane;
+    auto issue = [&](int per) {
+        const int r0 = per * RL;
+        if (r0 < mmax) {
+            T *dst = stage + (per & 1) * CH * 32;
+            const T *src = shs + (int64_t)r0 * RL * 32;
+            for (int i = tid; i < CH * 32 / PER16; i += 128) cp_async16(dst + PER16 * i, src + PER16 * i);
+        }
+        cp_async_commit();
+    };
+    issue(1);
+    // e[delta][j]: entry (delta + j, j) of the window, for the owned diagonals
+    T e[RL][RL];
+    StaticFor<0, RL>::run([&](auto Dc) {
+        constexpr int D = decltype(Dc)::value;
+        if constexpr (band4_owner(W, D) == Q) {
+#pragma unroll
+            for (int j = 0; j + D <= W; ++j) e[D][j] = D + j < m ? band[((int64_t)(D + j) * RL + D) * 32] : T(0);
+        }
+    });
+    bool bad = false;
+    int info = 0;
+    T d = T(0);
+    if constexpr (Q == 0) {
+        d = e[0][0];
+        bad = m > 0 && !(d > T(0));
+        info = bad ? 1 : 0;
+        rss[lane] = band_rsqrt(d);
+    }
+    band4_sync();
+    T rs = rss[lane];
+    const int PW = mmax / RL;
+    for (int p = 0; p <= PW; ++p) {
+        issue(p + 2);
+        cp_async_wait<1>();
+        band4_sync();  // period p + 1 has landed for every thread's copies
+        const T *src = stage + ((p + 1) & 1) * CH * 32 + lane;
+        T *lrow = band + (int64_t)p * RL * RL * 32;
+        const int left = m - p * RL;
+#pragma unroll 1
+        for (int ph = 0; ph < RL; ++ph) {
+            const bool live = ph < left;
+            // A: L's column k
+            if (live) {
+                if constexpr (Q == 0) lrow[ph * RL * 32] = d * rs;
+                StaticFor<1, RL>::run([&](auto Dc) {
+                    constexpr int D = decltype(Dc)::value;
+                    if constexpr (band4_owner(W, D) == Q) {
+                        const T l = e[D][0] * rs;
+                        ls[D * 32 + lane] = l;
+                        lrow[((ph + D) * RL + D) * 32] = l;
+                    }
+                });
+            }
+            band4_sync();
+            // B: the updates, the next pivot, the shift
+            if (live) {
+                T lv[RL];
+#pragma unroll
+                for (int c = 1; c <= W; ++c) lv[c] = ls[c * 32 + lane];
+                if constexpr (Q == 0) {
+                    if constexpr (W >= 1) {
+                        const T dn = band_fma(-lv[1], lv[1], e[0][1]);
+                        rss[lane] = band_rsqrt(dn);
+                        e[0][1] = dn;
+                    }
+                }
+                StaticFor<0, RL>::run([&](auto Dc) {
+                    constexpr int D = decltype(Dc)::value;
+                    if constexpr (band4_owner(W, D) == Q) {
+#pragma unroll
+                        for (int j = (D == 0 ? 2 : 1); j + D <= W; ++j) e[D][j] = band_fma(-lv[D + j], lv[j], e[D][j]);
+#pragma unroll
+                        for (int j = 0; j + D < W; ++j) e[D][j] = e[D][j + 1];
+                        e[D][W - D] = src[(ph * RL + D) * 32];
+                    }
+                });
+                if constexpr (Q == 0) {
+                    d = e[0][0];
+                    if constexpr (W == 0) rss[lane] = band_rsqrt(d);
+                    const int k = p * RL + ph;
+                    const bool f = k + 1 < m && !(d > T(0));
+                    if (f && !bad) info = k + 2;
+                    bad |= f;
+                }
+            }
+            band4_sync();
+            rs = rss[lane];
+        }
+        // a lane whose pivot failed stops (every warp of it)
+        if constexpr (Q == 0) bads[lane] = bad ? 1 : 0;
+        band4_sync();
+        if (bads[lane]) m = 0;
+    }
+    cp_async_wait<0>();
+    return info;
+}
+
+template <class T, int W>
+__device__ __forceinline__ int band_lanes4_any(T *shs, int lane, int m, int mmax, unsigned char *smem) {
+    switch (threadIdx.x >> 5) {
+    case 0: return band_lanes4<T, W, 0>(shs, lane, m, mmax, smem);
+    case 1: return band_lanes4<T, W, 1>(shs, lane, m, mmax, smem);
+    case 2: return band_lanes4<T, W, 2>(shs, lane, m, mmax, smem);
+    default: return band_lanes4<T, W, 3>(shs, lane, m, mmax, smem);
+    }
 }
 
 template <int W>

@@ -333,9 +333,9 @@ struct sympix_plan_s {
     // 2 band pass and chunked border solve on a shadow of the arithmetic,
     // 3 (FP32) band and border CTAs of one cooperative launch for w <= 8, 2
     // for 9 <= w <= 12.  Defaults from measurement at l_max = 3000 (factor
-    // stage): FP64 0 (20.1 ms; 2: 23.4 ms), FP32 3, split FP32 2 (7.9 ms;
+    // stage): FP64 2 (12.9 ms; 0: 20.1 ms), FP32 3, split FP32 2 (6.0 ms;
     // 1: 30.2 ms).
-    int narrow_pref[3] = {0, 3, 2};
+    int narrow_pref[3] = {2, 3, 2};
     // DP-grid plans (k > 1): band blocks under tile adjacency
     bool tiles = false;
     std::vector<TileBlock> tile_blocks;

@@ -638,7 +638,7 @@ extern "C" int sympix_plan_option(sympix_plan_t pl, int option, double value) {
         if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != -1.0)
             return set_error(SYMPIX_EINVAL, "sympix_plan_option: narrow factor kernel is -1, 0, 1, 2 or 3");
         if (value == -1.0) {
-            pl->narrow_pref[SYMPIX_PREC_FP64] = 0;
+            pl->narrow_pref[SYMPIX_PREC_FP64] = 2;
             pl->narrow_pref[SYMPIX_PREC_FP32] = 3;
             pl->narrow_pref[SYMPIX_PREC_FP32X2] = 2;
         } else if (value == 2.0 || value == 3.0) {

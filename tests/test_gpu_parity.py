@@ -787,7 +787,7 @@ def test_narrow_factor_matches_earlier_kernels(S, dev, fprec):
     plan.set_narrow_factor(1)
     ib = S.sympix_factor_blocks(plan, b, precision=fprec).cpu().numpy()
     plan.set_narrow_factor(-1)
-    assert plan.narrow_kernels() == {"fp64": 0, "fp32": 3, "fp32x2": 2}
+    assert plan.narrow_kernels() == {"fp64": 2, "fp32": 3, "fp32x2": 2}
     assert np.array_equal(ia, ib) and np.all(ia == 0)
     A, B = a.cpu().numpy(), b.cpu().numpy()
     tol = {"fp64": 1e-13, "fp32x2": 1e-11, "fp32": 1e-5}[fprec]
