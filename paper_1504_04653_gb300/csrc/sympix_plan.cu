@@ -265,19 +265,24 @@ extern "C" int sympix_support(sympix_grid_t grid, int nops, const double *r_s, i
             if (!again) break;
         }
     }
-    // slots: levels 0..kmax-1 of every canonical pair (max over operators)
+    // slots: levels 0..kmax-1 of every canonical pair (max over operators);
+    // the same-ring pairs' slots first, so that the kernel table's warps that
+    // evaluate d (needed there only, unless blocks between rings are planned)
+    // are a leading range and the others skip d's multiply-adds as a whole
     int64_t nslots = 0;
-    for (int pi = 0; pi < npairs; ++pi) {
-        CanonPair &cp = pl->pairs[pi];
-        int kmax = 0;
-        for (int o = 0; o < nops; ++o) {
-            int m = pl->pair_mmax[(size_t)pi * nops + o];
-            if (m >= 0) kmax = std::max(kmax, m / 2 + 1);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int pi = 0; pi < npairs; ++pi) {
+            CanonPair &cp = pl->pairs[pi];
+            if ((cp.a == cp.b) != (pass == 0)) continue;
+            int kmax = 0;
+            for (int o = 0; o < nops; ++o) {
+                int m = pl->pair_mmax[(size_t)pi * nops + o];
+                if (m >= 0) kmax = std::max(kmax, m / 2 + 1);
+            }
+            cp.kmax = kmax;
+            cp.slot0 = nslots;
+            nslots += kmax;
         }
-        cp.kmax = kmax;
-        cp.slot0 = nslots;
-        nslots += kmax;
-    }
     pl->nslots = nslots;
     if ((rc = pl->d_pairs.upload(pl->pairs)) || (rc = pl->d_slot_u.alloc(std::max<int64_t>(nslots, 1))) ||
         (rc = pl->d_slot_pair.alloc(std::max<int64_t>(nslots, 1))))

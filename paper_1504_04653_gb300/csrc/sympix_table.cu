@@ -85,24 +85,39 @@ __global__ void __launch_bounds__(128) k_table(int64_t nslots, int nops_total, i
                 }
         }
     }
-    for (int l = 1; l < lmax; ++l) {  // dlt = E_l on entry (E_1 = -u)
-        const double a = rec[2 * l], r = rec[2 * l + 1];
+    // the recurrence; a warp none of whose slots needs d (the plan puts the
+    // same-ring slots first) leaves d's multiply-adds out altogether
+    auto recur = [&](auto HASDc) {
+        constexpr bool HASD = decltype(HASDc)::value;
+        for (int l = 1; l < lmax; ++l) {  // dlt = E_l on entry (E_1 = -u)
+            const double a = rec[2 * l], r = rec[2 * l + 1];
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            dlt[j] = fma(a, u[j] * p[j], dlt[j]);
-            p[j] = fma(dlt[j], r, p[j]);
-        }
-#pragma unroll
-        for (int o = 0; o < NOPS; ++o)
-            if (o < nops) {
-                const double c = cb[(op0 + o) * L1 + l + 1], e = cd[(op0 + o) * L1 + l + 1];
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    sb[j][o] = fma(c, p[j], sb[j][o]);
-                    if (same[j]) sd[j][o] = fma(e, p[j], sd[j][o]);
-                }
+            for (int j = 0; j < J; ++j) {
+                dlt[j] = fma(a, u[j] * p[j], dlt[j]);
+                p[j] = fma(dlt[j], r, p[j]);
             }
-    }
+#pragma unroll
+            for (int o = 0; o < NOPS; ++o)
+                if (o < nops) {
+                    const double c = cb[(op0 + o) * L1 + l + 1];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) sb[j][o] = fma(c, p[j], sb[j][o]);
+                    if constexpr (HASD) {
+                        const double e = cd[(op0 + o) * L1 + l + 1];
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            if (same[j]) sd[j][o] = fma(e, p[j], sd[j][o]);
+                    }
+                }
+        }
+    };
+    bool anyd = false;
+#pragma unroll
+    for (int j = 0; j < J; ++j) anyd |= same[j];
+    if (__any_sync(0xffffffffu, anyd))
+        recur(std::true_type{});
+    else
+        recur(std::false_type{});
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         if (!ok[j]) continue;
