@@ -373,7 +373,7 @@ TRAFFIC = {
         799488, "e053756e1e7a",
         "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass over the bench's own mixed step"),
     ("lmax3000_fwhm5", "fp32:fp32", "k_f32_split_w8"): (
-        1555681024, "fb1d0ab24049",
+        1555681024, "ecc07086edd3",
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_f32_split<8,256,2> (759.2 + 796.5 MB), one pass "
         "over the bench's own mixed step (--steps 1 --warmup 1 --no-autotune), the timed step's launch"),
 }

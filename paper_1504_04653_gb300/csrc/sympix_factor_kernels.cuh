@@ -117,11 +117,6 @@ constexpr int kChunk = 16;  // band rows per staged chunk
 // index is static.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -592,20 +587,6 @@ struct F32BandDispatch<0, T> {
     __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage, float floor,
                               volatile int *prog = nullptr) {
         return w == 0 ? band_lanes<T, 0>(shs, lane, m, mmax, stage, floor, prog) : -1;
-    }
-};
-
-template <int W, class T>
-struct ExactBandDispatch {
-    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage) {
-        if (w == W) return band_lanes_loop<T, W>(shs, lane, m, mmax, stage);
-        return ExactBandDispatch<W - 1, T>::run(w, shs, lane, m, mmax, stage);
-    }
-};
-template <class T>
-struct ExactBandDispatch<0, T> {
-    __device__ static int run(int w, T *shs, int lane, int m, int mmax, T *stage) {
-        return w == 0 ? band_lanes_loop<T, 0>(shs, lane, m, mmax, stage) : -1;
     }
 };
 
