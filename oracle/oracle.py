@@ -84,6 +84,12 @@ def lib():
         L.sympix_oracle_guarded_radius.restype = ctypes.c_double
         L.sympix_oracle_guarded_radius.argtypes = [ctypes.c_int, _dptr, _i32ptr, ctypes.c_double,
                                                    ctypes.c_int, ctypes.c_int, _dptr]
+        L.sympix_oracle_degrade.restype = ctypes.c_long
+        L.sympix_oracle_degrade.argtypes = [ctypes.c_int, ctypes.c_long, _dptr, _dptr, _dptr, ctypes.c_int, _dptr,
+                                            _i32ptr, _dptr, _i64ptr, _i32ptr, _dptr]
+        L.sympix_oracle_block_y2.restype = ctypes.c_long
+        L.sympix_oracle_block_y2.argtypes = [_dptr, _i32ptr, ctypes.c_int, ctypes.c_int, _dptr, _i32ptr, _i64ptr,
+                                             _i32ptr, ctypes.c_int, _dptr, _dptr, ctypes.c_double, _dptr, _dptr]
         _lib = L
     return _lib
 
@@ -326,3 +332,54 @@ def cholesky(A: np.ndarray):
     L = np.zeros_like(A)
     info = lib().sympix_oracle_cholesky(n, _p(A, _dptr), _p(L, _dptr))
     return L, int(info)
+
+
+# -- Y2 != Y1 (Sec. 4.2, Eq. substitution, Eq. degrade) --------------------------
+
+def degrade(lmax2: int, obs_theta, obs_phi, obs_val, g2: dict) -> np.ndarray:
+    """Eq. degrade: theta_2 = W_2 Y_2 Y_obs^T theta on grid g2 (its pixel numbering),
+    Y_obs^T the unweighted adjoint synthesis at the observation points, lmax2 the
+    band limit of Y_2, W_2 the quadrature weights of g2 (ring weight x 2 pi / n)."""
+    th, ph, v = _f64(obs_theta), _f64(obs_phi), _f64(obs_val)
+    assert th.shape == ph.shape == v.shape
+    t2 = _f64(g2["theta"])
+    nr = np.ascontiguousarray(g2["nring"], dtype=np.int32)
+    w = _f64(g2["weight"]) if "weight" in g2 else gl_weights(t2)
+    off = np.ascontiguousarray(g2["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g2["ring_stride"], dtype=np.int32)
+    out = np.zeros(int(g2["npix"]), dtype=np.float64)
+    n = lib().sympix_oracle_degrade(int(lmax2), len(v), _p(th, _dptr), _p(ph, _dptr), _p(v, _dptr), int(g2["nrings"]),
+                                    _p(t2, _dptr), _p(nr, _i32ptr), _p(w, _dptr), _p(off, _i64ptr), _p(st, _i32ptr),
+                                    _p(out, _dptr))
+    assert n == int(nr.sum())
+    return out
+
+
+def block_y2(g1: dict, j: int, g2: dict, bl, dl, r_s: float, ninv2):
+    """Block of ring j of grid g1 with B^ = Y_2 B Y_1^T: the noise ninv2 lives on the
+    pixels of grid g2.  Returns (dense block, triples summed)."""
+    n = int(g1["nring"][j])
+    M = np.zeros((n, n), dtype=np.float64)
+    t1 = _f64(g1["theta"])
+    n1 = np.ascontiguousarray(g1["nring"], dtype=np.int32)
+    t2 = _f64(g2["theta"])
+    n2 = np.ascontiguousarray(g2["nring"], dtype=np.int32)
+    off = np.ascontiguousarray(g2["ring_offset"], dtype=np.int64)
+    st = np.ascontiguousarray(g2["ring_stride"], dtype=np.int32)
+    b, d, nv = _f64(bl), _f64(dl), _f64(ninv2)
+    assert len(nv) == int(g2["npix"]) and len(b) == len(d)
+    tr = lib().sympix_oracle_block_y2(_p(t1, _dptr), _p(n1, _i32ptr), int(j), int(g2["nrings"]), _p(t2, _dptr),
+                                      _p(n2, _i32ptr), _p(off, _i64ptr), _p(st, _i32ptr), len(b) - 1, _p(b, _dptr),
+                                      _p(d, _dptr), float(r_s), _p(nv, _dptr), _p(M, _dptr))
+    return M, int(tr)
+
+
+def gl_grid(nrings: int, n: int) -> dict:
+    """A Gauss-Legendre grid with the same count n on every ring, numbered ring by
+    ring (a quadrature that is exact for band limit 2 nrings - 1 in cos theta and
+    n - 1 in longitude): the exact auxiliary grid for Eq. degrade."""
+    theta = gl_theta(nrings)
+    nring = np.full(nrings, n, dtype=np.int32)
+    return dict(lmax=None, k=1, nrings=nrings, theta=theta, nring=nring, weight=gl_weights(theta),
+                ring_offset=np.arange(nrings, dtype=np.int64) * n, ring_stride=np.ones(nrings, dtype=np.int32),
+                npix=nrings * n)

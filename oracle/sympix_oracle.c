@@ -24,7 +24,10 @@
  *     operators, Sec. 4.2);
  *   - a block is one ring (tile size k = 1); its entries are
  *     D^_qr + sum_p B^_pq N^-1_p B^_pr over pixels p of the same grid
- *     (Eq. Dhat with Y2 = Y1).
+ *     (Eq. Dhat with Y2 = Y1), or, for Y2 != Y1, over the pixels of an
+ *     auxiliary grid carrying the noise of Eq. degrade;
+ *   - in Eq. degrade, N_2^-1 is built from theta_2 as N^-1 is from theta:
+ *     here both are the diagonal itself (N^-1 = diag(theta)).
  */
 #include <math.h>
 #include <stdint.h>
@@ -721,5 +724,103 @@ long sympix_oracle_band_block(int nrings, const double *theta, const int32_t *nr
 #undef BAND_ROW
     free(idx);
     free(val);
+    return triples;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Y2 != Y1: the noise on an auxiliary grid (Sec. 4.2, Eq. substitution,     */
+/* Eq. degrade)                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* 1 - cos of the angle between (t1, f1) and (t2, f2), by the haversine form:
+ * sin^2(gamma/2) = sin^2(dt/2) + sin t1 sin t2 sin^2(df/2). */
+static double u_angles(double t1, double f1, double t2, double f2)
+{
+    double a = sin(0.5 * (t1 - t2)), b = sin(0.5 * (f1 - f2));
+    return 2.0 * (a * a + sin(t1) * sin(t2) * b * b);
+}
+
+/* Eq. degrade: theta_2 = W_2 Y_2 Y_obs^T theta.  Y_obs^T theta is the
+ * unweighted adjoint synthesis a_lm = sum_i Y_lm(n_i) theta_i over the
+ * observation points i; Y_2 synthesises a_lm (l <= lmax2) on the auxiliary
+ * grid; W_2 multiplies pixel p by its quadrature weight w_p (the weight of its
+ * ring in cos theta times 2 pi / n_ring).  The sum over m is the addition
+ * theorem, so
+ *   theta_2[p] = w_p sum_i theta_i K(n_p . n_i),
+ *   K(x) = sum_{l <= lmax2} (2l+1)/(4 pi) P_l(x)
+ * (Eq. addition-theorem with every coefficient 1), evaluated per pair.
+ * Grid 2: nrings2 rings at theta2 with nring2 pixels each (pixel c at
+ * phi = 2 pi (c + 1/2) / n), ring weights wring2, pixel numbering
+ * ring_offset2 + c * ring_stride2.  Observation points: (obs_theta,
+ * obs_phi) with values obs_val.  Returns the pixels written, -1 on
+ * allocation failure. */
+long sympix_oracle_degrade(int lmax2, long nobs, const double *obs_theta, const double *obs_phi,
+                           const double *obs_val, int nrings2, const double *theta2, const int32_t *nring2,
+                           const double *wring2, const int64_t *ring_offset2, const int32_t *ring_stride2,
+                           double *out)
+{
+    double *ones = (double *)malloc(sizeof(double) * (size_t)(lmax2 + 1));
+    if (!ones) return -1;
+    for (int l = 0; l <= lmax2; ++l) ones[l] = 1.0;
+    long written = 0;
+    for (int rho = 0; rho < nrings2; ++rho) {
+        int n = nring2[rho];
+        double w = wring2[rho] * 2.0 * ORACLE_PI / (double)n;
+        for (long c = 0; c < n; ++c) {
+            double phi = 2.0 * ORACLE_PI * ((double)c + 0.5) / (double)n;
+            double s = 0.0;
+            for (long i = 0; i < nobs; ++i)
+                s += obs_val[i] * sympix_oracle_kernel_u(lmax2, ones, u_angles(theta2[rho], phi, obs_theta[i], obs_phi[i]));
+            out[ring_offset2[rho] + c * (int64_t)ring_stride2[rho]] = w * s;
+            ++written;
+        }
+    }
+    free(ones);
+    return written;
+}
+
+/* Eq. system-rewritten and Eq. Dhat with B^ = Y_2 B Y_1^T: the block of ring
+ * j of grid 1 (dense n_j x n_j, row-major), with the noise N_2^-1 = ninv2 on
+ * the pixels p of grid 2:
+ *   M_qr = [u_qr <= u_s] d(1-u_qr)
+ *        + sum over pixels p of grid 2 with u_pq <= u_s and u_pr <= u_s of
+ *          b(1-u_pq) N2^-1_p b(1-u_pr).
+ * With grid 2 = grid 1 this is sympix_oracle_block.  Returns the triples
+ * summed, -1 on allocation failure. */
+long sympix_oracle_block_y2(const double *theta1, const int32_t *nring1, int j, int nrings2,
+                            const double *theta2, const int32_t *nring2, const int64_t *ring_offset2,
+                            const int32_t *ring_stride2, int lmax, const double *bl, const double *dl,
+                            double r_s, const double *ninv2, double *M)
+{
+    int n = nring1[j];
+    double us = support_u(r_s);
+    memset(M, 0, sizeof(double) * (size_t)n * n);
+    for (long q = 0; q < n; ++q)
+        for (long r = 0; r < n; ++r) {
+            double u = sympix_oracle_u(theta1[j], n, q, theta1[j], n, r);
+            if (u <= us) M[q * n + r] += sympix_oracle_kernel_u(lmax, dl, u);
+        }
+    long triples = 0;
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * n);
+    double *val = (double *)malloc(sizeof(double) * n);
+    if (!idx || !val) { free(idx); free(val); return -1; }
+    for (int rho = 0; rho < nrings2; ++rho)
+        for (long p = 0; p < nring2[rho]; ++p) {
+            int cnt = 0;
+            for (long q = 0; q < n; ++q) {
+                double u = sympix_oracle_u(theta1[j], n, q, theta2[rho], nring2[rho], p);
+                if (u <= us) {
+                    idx[cnt] = (int32_t)q;
+                    val[cnt] = sympix_oracle_kernel_u(lmax, bl, u);
+                    ++cnt;
+                }
+            }
+            double np = ninv2[ring_offset2[rho] + p * (int64_t)ring_stride2[rho]];
+            for (int x = 0; x < cnt; ++x)
+                for (int y = 0; y < cnt; ++y)
+                    M[(size_t)idx[x] * n + idx[y]] += val[x] * np * val[y];
+            triples += (long)cnt * cnt;
+        }
+    free(idx); free(val);
     return triples;
 }
